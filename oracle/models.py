@@ -1,0 +1,264 @@
+"""Oracle Hamiltonian builders for the synthetic workloads (test infrastructure only).
+
+Sec. 3 of the paper builds H from an operator expression: apply the operator to
+every basis state and store each resulting coefficient, with the map from a state
+to its index held in a hash table (Sec. 4).  The workloads are spin chains and
+number-conserving bosons; their parameters come from the ``workloads`` module.
+
+Matrix convention (the standard one): H[i, j] = <i|H|j>, stored as CSR with
+ascending columns in every row and the diagonal always stored.  Values are built
+with single roundings in a fixed order so that an independent implementation
+following the same definitions reproduces them bit for bit:
+
+* spin chains: sigma^z_i = 1 - 2 bit_i(state);
+* TFIM diagonal: acc = 0; for bonds b = 0..L-2: acc += -J_b s_b s_{b+1};
+  off-diagonal at state ^ (1 << i): -h_i;
+* XXZ-DM diagonal: acc = 0; for bonds b: acc += (delta / 4) s_b s_{b+1}; then for
+  sites i: acc += (hz_i / 2) s_i.  Bond b joins sites b and (b+1) mod L.  A row
+  whose bond b has spin b up and spin b+1 down gets (hop_b / 2) at the state with
+  both flipped; the reverse configuration gets conj(hop_b) / 2;
+* bosons: basis = occupation tuples (n_0..n_{K-1}) summing to N, in descending
+  lexicographic order starting at (N, 0, ..., 0); the row of state n' holds
+  sum_i U_i (n'_i)^2 on the diagonal (accumulated in mode order) and, for every
+  ordered pair i != j with n'_i >= 1, the entry c_ij sqrt(n'_i) sqrt(n'_j + 1)
+  at the column of n' - e_i + e_j (c_ji = conj(c_ij)).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse
+
+
+@dataclass
+class CSR:
+    d: int
+    rowptr: np.ndarray   # int64, d + 1
+    col: np.ndarray      # int64, nnz
+    val: np.ndarray      # complex128, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_scipy(self):
+        return scipy.sparse.csr_matrix((self.val, self.col, self.rowptr), shape=(self.d, self.d))
+
+    def row(self, r: int):
+        b, e = int(self.rowptr[r]), int(self.rowptr[r + 1])
+        return self.col[b:e], self.val[b:e]
+
+
+def coo_to_csr(d: int, rows, cols, vals) -> CSR:
+    """COO triplets to CSR: order by (row, col) keeping input order among equal
+    keys, then add duplicates left to right in that order.  Explicit zeros stay."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.complex128)
+    order = np.lexsort((cols, rows))                  # stable: ties keep input order
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    if rows.size:
+        new = np.ones(rows.size, dtype=bool)
+        new[1:] = (rows[1:] != rows[:-1]) | (cols[1:] != cols[:-1])
+        seg = np.cumsum(new) - 1
+        out_val = np.zeros(int(seg[-1]) + 1, dtype=np.complex128)
+        np.add.at(out_val, seg, vals)                 # unbuffered, in index order
+        out_row, out_col = rows[new], cols[new]
+    else:
+        out_val = np.zeros(0, dtype=np.complex128)
+        out_row = out_col = np.zeros(0, dtype=np.int64)
+    rowptr = np.zeros(d + 1, dtype=np.int64)
+    np.add.at(rowptr, out_row + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return CSR(d, rowptr, out_col, out_val)
+
+
+def _sz_signs(L: int, r: np.ndarray):
+    return [1.0 - 2.0 * ((r >> i) & 1).astype(np.float64) for i in range(L)]
+
+
+def tfim_csr(p: dict) -> CSR:
+    """Transverse-field Ising chain with open boundary (see module docstring)."""
+    L = p["L"]
+    J, hx = p["J"], p["h"]
+    d = 1 << L
+    r = np.arange(d, dtype=np.int64)
+    s = _sz_signs(L, r)
+    diag = np.zeros(d)
+    for b in range(L - 1):
+        diag = diag + (-J[b]) * (s[b] * s[b + 1])
+    rows = [r]
+    cols = [r]
+    vals = [diag.astype(np.complex128)]
+    for i in range(L):
+        rows.append(r)
+        cols.append(r ^ (1 << i))
+        vals.append(np.full(d, -hx[i], dtype=np.complex128))
+    return coo_to_csr(d, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def xxzdm_csr(p: dict) -> CSR:
+    """XXZ chain with Dzyaloshinskii-Moriya phases (see module docstring)."""
+    L, pbc, delta = p["L"], p["pbc"], p["delta"]
+    hop_re, hop_im, hz = p["hop_re"], p["hop_im"], p["hz"]
+    if pbc and L < 3:
+        raise ValueError("periodic XXZ chain needs L >= 3")
+    nb = L if pbc else L - 1
+    d = 1 << L
+    r = np.arange(d, dtype=np.int64)
+    s = _sz_signs(L, r)
+    diag = np.zeros(d)
+    for b in range(nb):
+        diag = diag + (delta * 0.25) * (s[b] * s[(b + 1) % L])
+    for i in range(L):
+        diag = diag + (hz[i] * 0.5) * s[i]
+    rows = [r]
+    cols = [r]
+    vals = [diag.astype(np.complex128)]
+    for b in range(nb):
+        a, c = b, (b + 1) % L
+        bit_a = (r >> a) & 1
+        bit_c = (r >> c) & 1
+        mask = (1 << a) | (1 << c)
+        up_down = (bit_a == 0) & (bit_c == 1)        # spin a up, spin a+1 down
+        down_up = (bit_a == 1) & (bit_c == 0)
+        ra = r[up_down]
+        rows.append(ra)
+        cols.append(ra ^ mask)
+        vals.append(np.full(ra.size, complex(0.5 * hop_re[b], 0.5 * hop_im[b])))
+        rb = r[down_up]
+        rows.append(rb)
+        cols.append(rb ^ mask)
+        vals.append(np.full(rb.size, complex(0.5 * hop_re[b], -(0.5 * hop_im[b]))))
+    return coo_to_csr(d, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+# ---------------------------------------------------------------- bosons
+
+def bose_basis(K: int, N: int):
+    """All occupation tuples of K modes with N bosons, descending lexicographic."""
+    out = []
+    cur = [0] * K
+
+    def rec(pos: int, rem: int):
+        if pos == K - 1:
+            cur[pos] = rem
+            out.append(tuple(cur))
+            return
+        for a in range(rem, -1, -1):
+            cur[pos] = a
+            rec(pos + 1, rem - a)
+
+    rec(0, N)
+    return out
+
+
+class BoseBasis:
+    """Basis list plus the hash table state -> index (Sec. 3, eq. findIndices; Sec. 4)."""
+
+    def __init__(self, K: int, N: int):
+        self.K, self.N = K, N
+        self.states = bose_basis(K, N)
+        self.index = {s: i for i, s in enumerate(self.states)}
+
+    def __len__(self):
+        return len(self.states)
+
+
+def _pair(K: int, i: int, j: int) -> int:
+    """Position of c_ij (i < j) in the (i-major, j-minor) table."""
+    return i * K - i * (i + 1) // 2 + (j - i - 1)
+
+
+def bose_row(p: dict, basis: BoseBasis, r: int):
+    """Columns (ascending) and values of row r of the bosonic Hamiltonian."""
+    K = p["K"]
+    c_re, c_im, U = p["c_re"], p["c_im"], p["U"]
+    n = basis.states[r]
+    acc = 0.0
+    for i in range(K):
+        acc = acc + U[i] * float(n[i] * n[i])
+    entries = [(r, complex(acc, 0.0))]
+    for i in range(K):
+        if n[i] == 0:
+            continue
+        for j in range(K):
+            if j == i:
+                continue
+            src = list(n)
+            src[i] -= 1
+            src[j] += 1
+            col = basis.index[tuple(src)]
+            amp = math.sqrt(float(n[i])) * math.sqrt(float(n[j] + 1))
+            if i < j:
+                cr, ci = c_re[_pair(K, i, j)], c_im[_pair(K, i, j)]
+            else:
+                cr, ci = c_re[_pair(K, j, i)], -c_im[_pair(K, j, i)]
+            entries.append((col, complex(cr * amp, ci * amp)))
+    entries.sort(key=lambda e: e[0])
+    return (np.array([e[0] for e in entries], dtype=np.int64),
+            np.array([e[1] for e in entries], dtype=np.complex128))
+
+
+def bose_csr(p: dict, basis: BoseBasis | None = None) -> CSR:
+    """Full bosonic CSR, one row at a time (small K, N only)."""
+    basis = basis or BoseBasis(p["K"], p["N"])
+    d = len(basis)
+    cols, vals, lens = [], [], []
+    for r in range(d):
+        c, v = bose_row(p, basis, r)
+        cols.append(c)
+        vals.append(v)
+        lens.append(c.size)
+    rowptr = np.zeros(d + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(lens)
+    return CSR(d, rowptr, np.concatenate(cols), np.concatenate(vals))
+
+
+def build(p: dict) -> CSR:
+    """Dispatch on the parameter table's model name."""
+    if p["model"] == "tfim":
+        return tfim_csr(p)
+    if p["model"] == "xxzdm":
+        return xxzdm_csr(p)
+    if p["model"] == "bose":
+        return bose_csr(p)
+    raise ValueError(p["model"])
+
+
+def spin_row(p: dict, r: int):
+    """Row r of a spin-chain Hamiltonian, built entry by entry (for sampled checks
+    at sizes where the vectorised builders would be slow)."""
+    L = p["L"]
+    s = [1.0 - 2.0 * ((r >> i) & 1) for i in range(L)]
+    entries = []
+    if p["model"] == "tfim":
+        acc = 0.0
+        for b in range(L - 1):
+            acc = acc + (-p["J"][b]) * (s[b] * s[b + 1])
+        entries.append((r, complex(acc, 0.0)))
+        for i in range(L):
+            entries.append((r ^ (1 << i), complex(-p["h"][i], 0.0)))
+    elif p["model"] == "xxzdm":
+        nb = L if p["pbc"] else L - 1
+        acc = 0.0
+        for b in range(nb):
+            acc = acc + (p["delta"] * 0.25) * (s[b] * s[(b + 1) % L])
+        for i in range(L):
+            acc = acc + (p["hz"][i] * 0.5) * s[i]
+        entries.append((r, complex(acc, 0.0)))
+        for b in range(nb):
+            a, c = b, (b + 1) % L
+            ba, bc = (r >> a) & 1, (r >> c) & 1
+            mask = (1 << a) | (1 << c)
+            if ba == 0 and bc == 1:
+                entries.append((r ^ mask, complex(0.5 * p["hop_re"][b], 0.5 * p["hop_im"][b])))
+            elif ba == 1 and bc == 0:
+                entries.append((r ^ mask, complex(0.5 * p["hop_re"][b], -(0.5 * p["hop_im"][b]))))
+    else:
+        raise ValueError(p["model"])
+    entries.sort(key=lambda e: e[0])
+    return (np.array([e[0] for e in entries], dtype=np.int64),
+            np.array([e[1] for e in entries], dtype=np.complex128))

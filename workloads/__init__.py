@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs for the Krylov time-evolution workloads.
+
+This module is the one place both the CUDA path and the CPU oracle take their
+inputs from.  It draws random numbers and turns them into model parameter tables
+and initial vectors; it holds none of the method's arithmetic (no Lanczos, no
+Hamiltonian assembly, no basis ordering, no quadrature).
+
+Random numbers come from splitmix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used as a counter-based generator:
+output i of stream ``seed`` is ``mix(seed + (i + 1) * 0x9E3779B97F4A7C15)``.
+Uniforms take the top 53 bits.  Everything is plain numpy uint64/float64
+arithmetic, so the tables are identical on x86 and Arm hosts.
+
+Conventions shared by the model builders on both sides (the definitions of the
+workloads, stated once here so both sides read the same words):
+
+* spin chains: basis index bit i = 1 means spin i points down (sigma^z_i = -1),
+  bit i = 0 means up;
+* complex hopping amplitudes are handed over as (re, im) pairs, already formed
+  from their random phases here, so the builders multiply and add only.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n outputs of the counter-based splitmix64 stream ``seed`` (uint64)."""
+    i = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """n uniforms on [lo, hi) from stream ``seed`` (53-bit resolution)."""
+    u = (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def complex_gaussian(seed: int, d: int) -> np.ndarray:
+    """d standard complex Gaussians (Box-Muller on 2d uniforms)."""
+    u = uniform(seed, 2 * d)
+    u1, u2 = u[:d], u[d:]
+    r = np.sqrt(-2.0 * np.log1p(-u1))
+    return r * np.cos(2.0 * np.pi * u2) + 1j * (r * np.sin(2.0 * np.pi * u2))
+
+
+def random_state(seed: int, d: int) -> np.ndarray:
+    """Normalised random complex128 initial vector of length d."""
+    g = complex_gaussian(seed, d)
+    return g / np.linalg.norm(g)
+
+
+def basis_state(d: int, index: int) -> np.ndarray:
+    """complex128 unit vector e_index of length d."""
+    v = np.zeros(d, dtype=np.complex128)
+    v[index] = 1.0
+    return v
+
+
+# ---------------------------------------------------------------- model tables
+
+def tfim_params(L: int, seed: int) -> dict:
+    """Transverse-field Ising chain, open boundary.
+
+    H = -sum_{i<L-1} J_i s^z_i s^z_{i+1} - sum_i h_i s^x_i  (Pauli matrices),
+    J_i, h_i ~ U[0.5, 1.5).
+    """
+    u = uniform(seed, 2 * L - 1, 0.5, 1.5)
+    return {"model": "tfim", "L": L, "J": u[: L - 1].copy(), "h": u[L - 1:].copy()}
+
+
+def xxzdm_params(L: int, seed: int, delta: float = 0.8, pbc: bool = True) -> dict:
+    """XXZ chain with a Dzyaloshinskii-Moriya phase on each bond.
+
+    H = sum_b [ 1/2 (e^{i phi_b} S^+_b S^-_{b+1} + h.c.) + delta S^z_b S^z_{b+1} ]
+        + sum_i hz_i S^z_i     (spin-1/2 operators, S = sigma/2),
+    phi_b ~ U[0, 2 pi), hz_i ~ U[-1, 1).  Bond b couples sites b and (b+1) mod L;
+    there are L bonds with a periodic boundary, L-1 with an open one.
+    """
+    nb = L if pbc else L - 1
+    u = uniform(seed, nb + L)
+    phi = 2.0 * np.pi * u[:nb]
+    return {
+        "model": "xxzdm", "L": L, "pbc": bool(pbc), "delta": float(delta),
+        "hop_re": np.cos(phi), "hop_im": np.sin(phi),
+        "hz": -1.0 + 2.0 * u[nb:],
+    }
+
+
+def bose_params(K: int, N: int, seed: int) -> dict:
+    """Number-conserving bosons on K modes with N particles.
+
+    H = sum_{i != j} c_ij a_i^dag a_j + sum_i U_i n_i^2,  c_ji = conj(c_ij),
+    |c_ij| ~ U[0,1), arg c_ij ~ U[0, 2 pi), U_i ~ U[0, 2).  The table lists c_ij
+    for i < j in (i-major, j-minor) order.
+    """
+    npair = K * (K - 1) // 2
+    u = uniform(seed, 2 * npair + K)
+    mag = u[:npair]
+    theta = 2.0 * np.pi * u[npair: 2 * npair]
+    return {
+        "model": "bose", "K": K, "N": N,
+        "c_re": mag * np.cos(theta), "c_im": mag * np.sin(theta),
+        "U": 2.0 * u[2 * npair:],
+    }
+
+
+def neel_index(L: int) -> int:
+    """Basis index of the Neel state (spin i up for even i, down for odd i)."""
+    return sum(1 << i for i in range(1, L, 2))
+
+
+def bose_dim(K: int, N: int) -> int:
+    """Number of occupation tuples of K modes holding N bosons, C(N+K-1, N)."""
+    return math.comb(N + K - 1, N)
+
+
+# ---------------------------------------------------------------- workloads
+
+def workload(name: str) -> dict:
+    """Named synthetic workloads (parameters, initial state and solve settings)."""
+    if name == "tfim_L12":
+        p = tfim_params(12, seed=1)
+        return {"name": name, "params": p, "d": 1 << 12, "v0": ("random", 101),
+                "t": 10.0, "m": 40, "tol": 1e-8}
+    if name == "xxzdm_L22":
+        p = xxzdm_params(22, seed=2)
+        return {"name": name, "params": p, "d": 1 << 22, "v0": ("index", neel_index(22)),
+                "t": 50.0, "m": 40, "tol": 1e-8}
+    if name == "xxzdm_L20":
+        p = xxzdm_params(20, seed=3)
+        return {"name": name, "params": p, "d": 1 << 20, "v0": ("random", 301),
+                "t": 50.0, "m": 40, "tol": 1e-8}
+    if name == "bose_K14_N10":
+        p = bose_params(14, 10, seed=4)
+        occ = tuple([1] * 10 + [0] * 4)
+        return {"name": name, "params": p, "d": bose_dim(14, 10), "v0": ("occupation", occ),
+                "t": 20.0, "m": 50, "tol": 1e-10}
+    raise KeyError(name)
+
+
+def initial_vector(spec, d: int, index_of=None) -> np.ndarray:
+    """Build the initial vector from a workload's ``v0`` spec.
+
+    ``index_of`` maps an occupation tuple to a basis index; it is supplied by the
+    caller (each side uses its own basis ordering).
+    """
+    kind, arg = spec
+    if kind == "random":
+        return random_state(arg, d)
+    if kind == "index":
+        return basis_state(d, arg)
+    if kind == "occupation":
+        if index_of is None:
+            raise ValueError("occupation initial state needs an index_of callable")
+        return basis_state(d, int(index_of(arg)))
+    raise ValueError(kind)
