@@ -1,0 +1,241 @@
+/*
+ * te.h -- C ABI of libte: restarted Krylov time evolution exp(-iHt)v on one GPU.
+ *
+ * The method is TimeEvolver's (arXiv 2205.15346): Lanczos vectors of a sparse
+ * Hermitian H (Sec. 2.1, eq. arnoldi), the a-posteriori error bound of
+ * eq. errorIntegral evaluated by adaptive tanh-sinh quadrature (Sec. 2.3, Sec. 4),
+ * the largest step allowed by eqs. errorRate and stepSize, the Krylov exponential
+ * of eq. krylovApproximation, and a restart from the result (Algorithm 1).
+ * Everything is complex128 / float64.
+ *
+ * Conventions for every call:
+ *   - Functions return te_status; 0 is TE_OK.  They never abort or throw.  After
+ *     an error te_last_error(ctx) holds a message owned by the context.
+ *   - Complex vectors are interleaved (re, im) float64 pairs, i.e. the memory
+ *     layout of C99 double complex / cuDoubleComplex / torch.complex128.
+ *   - Pointers are host pointers unless the call's flags contain TE_PTR_DEVICE,
+ *     in which case they are device pointers on the context's device.  Caller
+ *     buffers are borrowed for the duration of the call only (te_submit copies
+ *     its input vector before it returns).
+ *   - Work is issued on the context's stream.  Synchronous calls (te_build_*,
+ *     te_evolve, te_spmv, te_matrix_export) have finished on the device when
+ *     they return.
+ *   - Matrices are stored as CSR with int32 row pointers and column indices and
+ *     complex128 values (20 bytes per stored entry); nnz must stay below 2^31.
+ */
+#ifndef TE_H_
+#define TE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t te_status;
+#define TE_OK                  0
+#define TE_PENDING             1   /* te_poll: request not finished yet */
+#define TE_ERR_INVALID_ARG    -1   /* bad size, index out of range, bad option */
+#define TE_ERR_CUDA           -2   /* a CUDA runtime call failed (message has the CUDA error) */
+#define TE_ERR_OOM            -3   /* device or host allocation failed */
+#define TE_ERR_NOT_HERMITIAN  -4   /* TE_CHECK_HERMITIAN found H[i,j] != conj(H[j,i]) */
+#define TE_ERR_NOT_NORMALIZED -5   /* | ||v_in|| - 1 | > 1e-10 (Sec. 2.1 assumes ||v(0)|| = 1) */
+#define TE_ERR_STEP_UNDERFLOW -6   /* no step >= min_step_rel*|t| meets the error rate (e.g. m = 1) */
+#define TE_ERR_NONFINITE      -7   /* NaN or Inf in the input vector or in H */
+#define TE_ERR_TIMEOUT        -8   /* a bounded wait gave up (scheduler, device waits) */
+#define TE_ERR_CANCELLED      -9   /* request cancelled by te_cancel */
+#define TE_ERR_UNSUPPORTED   -10   /* valid request outside this build's limits (nnz >= 2^31, m > TE_M_MAX) */
+#define TE_ERR_INTERNAL      -11   /* eigensolver did not converge or another internal check failed */
+
+/* flags for pointer arguments and builders */
+#define TE_PTR_DEVICE        0x1u  /* pointer arguments are device pointers */
+#define TE_CHECK_HERMITIAN   0x2u  /* te_build_csr: verify H == H^dagger (relative 1e-13 of max |H_ij|) */
+#define TE_INPUT_IS_CSR      0x4u  /* te_build_csr: rows is a row pointer array of length d+1 */
+
+/* te_stats.flags */
+#define TE_WARN_ROUNDOFF     0x1u  /* d ||H||_1 eps > err_max (eq. numericalError; Sec. 2.4 list) */
+#define TE_WARN_QUAD         0x2u  /* an error integral did not reach quad_rel_tol within quad_max_levels (Sec. 4) */
+#define TE_FLAG_BREAKDOWN    0x4u  /* a lucky breakdown ended a Krylov space early (Sec. 2.4 step 1) */
+
+#define TE_M_MAX 128               /* largest Krylov dimension m */
+
+/* te_options.quad */
+#define TE_QUAD_TANH_SINH 0        /* adaptive double-exponential rule (default, Sec. 2.3) */
+#define TE_QUAD_GAUSS     1        /* non-adaptive Gauss-Legendre, gauss_n nodes (Sec. 4) */
+/* te_options.reorth */
+#define TE_REORTH_NONE 0           /* three-term recurrence of eq. arnoldi (default) */
+#define TE_REORTH_FULL 1           /* also classical Gram-Schmidt twice against all earlier vectors */
+/* te_options.flags */
+#define TE_OPT_PROFILE 0x10u       /* time every fused SpMV launch with CUDA events (te_stats.spmv_*) */
+
+/*
+ * Solver options.  te_default_options fills the defaults, which follow the
+ * paper: first step guess 0.1 and a 0.97 shrink of the previous step
+ * (Algorithm 1), tanh-sinh with relative tolerance 1e-3 and at most 15
+ * refinements (Sec. 4).  n_substeps (the paper's N_SUBSTEPS) is 10.
+ */
+typedef struct te_options {
+    int32_t  quad;             /* TE_QUAD_TANH_SINH or TE_QUAD_GAUSS */
+    int32_t  gauss_n;          /* Gauss nodes per interval, 2..64 (default 20) */
+    int32_t  n_substeps;       /* growth substeps per step, >= 1 (default 10) */
+    int32_t  reorth;           /* TE_REORTH_NONE or TE_REORTH_FULL */
+    double   t_step0;          /* first step guess (default 0.1) */
+    double   shrink;           /* factor on the previous step, in (0,1] (default 0.97) */
+    double   quad_rel_tol;     /* tanh-sinh stop: |I_k - I_{k-1}| <= tol |I_k| (default 1e-3) */
+    int32_t  quad_max_levels;  /* tanh-sinh refinements, 3..20 (default 15) */
+    int32_t  max_substeps;     /* cap on growth substeps per step (default 1000) */
+    double   min_step_rel;     /* underflow when a step falls below this * |t| (default 1e-13) */
+    uint32_t flags;            /* TE_PTR_DEVICE for v_in / v_out; TE_OPT_PROFILE */
+    int32_t  spmv_lanes;       /* lanes per CSR row in the SpMV (1..32, power of 2); 0 = automatic */
+} te_options;
+
+/* Per-solve report.  err_bound is the sum of the accepted step errors (the
+ * a-posteriori bound on ||v_out - exp(-iHt)v_in|| up to roundoff and the
+ * quadrature tolerance).  roundoff_est = d ||H||_1 2^-52 (eq. numericalError). */
+typedef struct te_stats {
+    int64_t  restarts;         /* Krylov spaces built */
+    int64_t  matvecs;          /* products H v */
+    int64_t  breakdowns;       /* lucky breakdowns */
+    int64_t  quad_warnings;    /* integrals stopped by quad_max_levels */
+    double   err_bound;
+    double   roundoff_est;
+    double   t_reached;        /* signed time reached (t unless an error stopped the solve) */
+    double   norm_in;          /* ||v_in|| */
+    uint32_t flags;            /* TE_WARN_*, TE_FLAG_* */
+    int32_t  m_used;           /* Krylov dimension used (min(m, d)) */
+    double   spmv_ms;          /* TE_OPT_PROFILE: summed CUDA-event time of fused SpMV launches */
+    int64_t  spmv_launches;    /* TE_OPT_PROFILE: launches summed in spmv_ms */
+    double   solve_ms;         /* host wall time of the call */
+} te_stats;
+
+typedef struct te_matrix_info {
+    int64_t d;                 /* dimension */
+    int64_t nnz;               /* stored entries */
+    double  norm1;             /* ||H||_1 = max absolute column sum (= max row sum for Hermitian H) */
+    int32_t max_row_nnz;
+    int32_t spmv_lanes;        /* lanes per row chosen for this matrix */
+} te_matrix_info;
+
+/* Synthetic model Hamiltonians built on the device (Sec. 3: the matrix of an
+ * operator expression in a number-state basis).  Parameter arrays are host
+ * pointers, read during the call. */
+#define TE_MODEL_TFIM  1  /* H = -sum_{b<L-1} a[b] Z_b Z_{b+1} - sum_i b[i] X_i, open chain, d = 2^L */
+#define TE_MODEL_XXZDM 2  /* H = sum_b [1/2 (e^{i phi_b} S+_b S-_{b+1} + h.c.) + delta Sz_b Sz_{b+1}]
+                             + sum_i c[i] Sz_i; e^{i phi_b} = a[b] + i b[b]; pbc -> L bonds, else L-1 */
+#define TE_MODEL_BOSE  3  /* H = sum_{i!=j} c_ij a_i^+ a_j + sum_i c[i] n_i^2 on K = L modes with N bosons;
+                             c_ij = a[p] + i b[p] for i<j, p in (i-major, j-minor) order, c_ji = conj(c_ij) */
+typedef struct te_model_desc {
+    int32_t model;             /* TE_MODEL_* */
+    int32_t L;                 /* spins (chains, 3..30) or modes K (bosons, 2..16) */
+    int32_t N;                 /* bosons: particles, 1..15 */
+    int32_t pbc;               /* XXZ-DM: 1 periodic (needs L >= 3), 0 open */
+    double  delta;             /* XXZ-DM anisotropy */
+    const double* a;           /* see the model comments */
+    const double* b;
+    const double* c;
+} te_model_desc;
+/* Basis conventions: spin chains use index bit i = 1 for spin i down
+ * (sigma^z_i = -1).  Bosonic states are occupation tuples (n_0..n_{K-1}) with
+ * sum N, indexed in descending lexicographic order from (N,0,...,0); on the
+ * device the tuple -> index map is a hash table (Sec. 4). */
+
+typedef struct te_ctx te_ctx;
+typedef struct te_matrix te_matrix;
+typedef struct te_request te_request;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * owned by the caller (NULL: the context creates and owns a non-blocking
+ * stream).  The context owns its device workspace (Krylov bases, reduction
+ * scratch, captured CUDA graphs) and frees it in te_destroy. */
+te_status te_create(te_ctx** out, int32_t device, void* cuda_stream);
+void te_destroy(te_ctx* ctx);
+const char* te_last_error(const te_ctx* ctx);
+const char* te_status_string(te_status s);
+void te_default_options(te_options* opt);
+/* Version string of the library (static storage). */
+const char* te_version(void);
+
+/* ---- matrices ----------------------------------------------------------- */
+
+/* Build H from COO triplets (row, col, value) -- or, with TE_INPUT_IS_CSR,
+ * from CSR arrays where rows[0..d] is the row pointer and n_entries = rows[d].
+ * Entries are ordered by (row, col); duplicates are added in input order;
+ * explicit zeros are kept.  vals holds 2*n_entries doubles (re, im).
+ * Errors: TE_ERR_INVALID_ARG (d < 1, an index outside [0, d), a non-monotone
+ * row pointer), TE_ERR_NONFINITE, TE_ERR_NOT_HERMITIAN (with TE_CHECK_HERMITIAN),
+ * TE_ERR_UNSUPPORTED (nnz >= 2^31 or d >= 2^31), TE_ERR_OOM.
+ * The library owns the result; release it with te_matrix_free. */
+te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t* rows,
+                       const int64_t* cols, const double* vals, uint32_t flags,
+                       te_matrix** out);
+
+/* Build a model Hamiltonian on the device (see TE_MODEL_*).  Rows hold ascending
+ * columns with the diagonal always stored.  Errors: TE_ERR_INVALID_ARG,
+ * TE_ERR_UNSUPPORTED (size limits), TE_ERR_OOM. */
+te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out);
+
+/* Index of a bosonic occupation tuple occ[0..K-1] in the TE_MODEL_BOSE basis
+ * (host-side ranking; TE_ERR_INVALID_ARG if the tuple is not in the basis). */
+te_status te_model_basis_index(const te_model_desc* desc, const int32_t* occ, int64_t* index);
+
+te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info);
+
+/* Copy the CSR arrays out: rowptr[d+1], col[nnz] (int32), val[2*nnz]
+ * (host buffers, or device buffers with TE_PTR_DEVICE).  Any pointer may be
+ * NULL to skip that array. */
+te_status te_matrix_export(te_ctx* ctx, const te_matrix* H, int32_t* rowptr, int32_t* col,
+                           double* val, uint32_t flags);
+
+/* Free a matrix (and any cached solver plans built for it). */
+void te_matrix_free(te_matrix* H);
+
+/* ---- products and solves ------------------------------------------------ */
+
+/* y = H x (Sec. 2.1: the sparse product that dominates each Lanczos step).
+ * x, y: complex128 vectors of length d, distinct buffers.  If x_dot_y is not
+ * NULL it receives Re <x, H x> (the energy of x).  Flags: TE_PTR_DEVICE. */
+te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y,
+                  double* x_dot_y, uint32_t flags);
+
+/* v_out = exp(-i H t) v_in to within err_max = tol (Algorithm 1).
+ * v_in must be normalised to 1e-10 (Sec. 2.1).  t < 0 evolves with -H for |t|
+ * (the reversal of Sec. 5); t = 0 copies v_in.  m is the Krylov dimension,
+ * 1 <= m <= TE_M_MAX, clamped to d.  tol > 0.  opt may be NULL (defaults);
+ * opt->flags & TE_PTR_DEVICE says whether v_in / v_out are device pointers.
+ * v_in and v_out may be the same buffer.  st may be NULL.
+ * Errors: TE_ERR_INVALID_ARG, TE_ERR_NOT_NORMALIZED, TE_ERR_NONFINITE,
+ * TE_ERR_STEP_UNDERFLOW (v_out then holds the state at st->t_reached),
+ * TE_ERR_UNSUPPORTED, TE_ERR_INTERNAL, TE_ERR_CUDA, TE_ERR_OOM. */
+te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
+                    int32_t m, const te_options* opt, double* v_out, te_stats* st);
+
+/* ---- asynchronous requests --------------------------------------------- */
+
+/* Queue a solve with the same meaning as te_evolve.  v_in is copied before the
+ * call returns.  The context's scheduler admits queued requests while their
+ * device footprint ((m+1) d 16 bytes plus reduction scratch) fits the
+ * context's memory budget and runs admitted requests concurrently, each on its
+ * own stream, one restart at a time.  H must outlive the request. */
+te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
+                    int32_t m, const te_options* opt, te_request** out);
+/* TE_PENDING while queued or running; otherwise the solve's status, with the
+ * result copied to v_out (host unless the submit options had TE_PTR_DEVICE) and
+ * stats to st (either may be NULL). */
+te_status te_poll(te_request* req, double* v_out, te_stats* st);
+/* Wait up to timeout_ms (< 0: no limit) for the request; returns as te_poll,
+ * TE_PENDING on timeout. */
+te_status te_wait(te_request* req, double timeout_ms, double* v_out, te_stats* st);
+/* Ask the scheduler to stop the request at its next restart boundary. */
+te_status te_cancel(te_request* req);
+/* Free a finished request (waits for it if it is still running). */
+void te_request_free(te_request* req);
+/* Bytes of device memory the scheduler may hold for running requests
+ * (default: 80% of the free memory at te_create). */
+te_status te_set_memory_budget(te_ctx* ctx, int64_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TE_H_ */

@@ -1,0 +1,554 @@
+// te_build.cu -- Hamiltonian matrices built on the device (Sec. 3 of arXiv 2205.15346).
+//
+// Sec. 3 forms H by applying the operator to every basis state and storing
+// each coefficient at (state, image state), with the state -> index map held in
+// a hash table (Sec. 4).  Here one thread builds one row: it applies the
+// operator to its basis state, looks the image states up, sorts the row by
+// column and writes it.  The stored matrix is the standard H[i,j] = <i|H|j>.
+//
+// Values are formed with explicitly rounded multiplies and adds in a fixed
+// order (the definitions are stated in te.h), so the arrays are reproducible
+// bit for bit by any implementation that follows the same definitions.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "te_internal.cuh"
+
+namespace {
+
+constexpr int kBoseMaxEntries = 1 + 15 * 15;   // diagonal + n_occupied (K - 1), K <= 16, N <= 15
+constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ double spin_sign(int64_t r, int i) {
+    return 1.0 - 2.0 * (double)((r >> i) & 1);
+}
+
+// ---------------------------------------------------------------- TFIM
+
+__global__ void k_build_tfim(int L, const double* __restrict__ J, const double* __restrict__ hx,
+                             int64_t d, int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                             double2* __restrict__ val) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    const int64_t w = L + 1;
+    rowptr[r] = (int32_t)(r * w);
+    if (r == d - 1) rowptr[d] = (int32_t)(d * w);
+    double acc = 0.0;
+    for (int b = 0; b < L - 1; ++b)
+        acc = __dadd_rn(acc, __dmul_rn(-J[b], spin_sign(r, b) * spin_sign(r, b + 1)));
+    int64_t pos = r * w;
+    for (int i = L - 1; i >= 0; --i)               // flips that lower the index, ascending
+        if ((r >> i) & 1) {
+            col[pos] = (int32_t)(r ^ (1ll << i));
+            val[pos] = make_double2(-hx[i], 0.0);
+            ++pos;
+        }
+    col[pos] = (int32_t)r;
+    val[pos] = make_double2(acc, 0.0);
+    ++pos;
+    for (int i = 0; i < L; ++i)                    // flips that raise the index, ascending
+        if (!((r >> i) & 1)) {
+            col[pos] = (int32_t)(r ^ (1ll << i));
+            val[pos] = make_double2(-hx[i], 0.0);
+            ++pos;
+        }
+}
+
+// ---------------------------------------------------------------- XXZ-DM
+
+__global__ void k_count_xxzdm(int L, int nb, int64_t d, int32_t* __restrict__ cnt) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    int c = 1;
+    for (int b = 0; b < nb; ++b) c += (int)(((r >> b) ^ (r >> ((b + 1) % L))) & 1);
+    cnt[r] = c;
+}
+
+__global__ void k_fill_xxzdm(int L, int nb, double delta, const double* __restrict__ hre,
+                             const double* __restrict__ him, const double* __restrict__ hz,
+                             int64_t d, const int32_t* __restrict__ rowptr,
+                             int32_t* __restrict__ col, double2* __restrict__ val) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    int32_t cs[32];
+    double2 vs[32];
+    double acc = 0.0;
+    const double dq = delta * 0.25;
+    for (int b = 0; b < nb; ++b)
+        acc = __dadd_rn(acc, __dmul_rn(dq, spin_sign(r, b) * spin_sign(r, (b + 1) % L)));
+    for (int i = 0; i < L; ++i) acc = __dadd_rn(acc, __dmul_rn(hz[i] * 0.5, spin_sign(r, i)));
+    int n = 0;
+    cs[n] = (int32_t)r;
+    vs[n] = make_double2(acc, 0.0);
+    ++n;
+    for (int b = 0; b < nb; ++b) {
+        const int a = b, c = (b + 1) % L;
+        const int ba = (int)((r >> a) & 1), bc = (int)((r >> c) & 1);
+        if (ba == bc) continue;
+        const int64_t tgt = r ^ ((1ll << a) | (1ll << c));
+        const double re = 0.5 * hre[b], im = 0.5 * him[b];
+        cs[n] = (int32_t)tgt;
+        vs[n] = (ba == 0) ? make_double2(re, im) : make_double2(re, -im);
+        ++n;
+    }
+    for (int i = 1; i < n; ++i) {                   // insertion sort by column
+        const int32_t kc = cs[i];
+        const double2 kv = vs[i];
+        int k = i - 1;
+        while (k >= 0 && cs[k] > kc) {
+            cs[k + 1] = cs[k];
+            vs[k + 1] = vs[k];
+            --k;
+        }
+        cs[k + 1] = kc;
+        vs[k + 1] = kv;
+    }
+    const int64_t p = rowptr[r];
+    for (int i = 0; i < n; ++i) {
+        col[p + i] = cs[i];
+        val[p + i] = vs[i];
+    }
+}
+
+// ---------------------------------------------------------------- bosons
+
+struct BoseTables {
+    int K, N;
+    unsigned long long comp[16][17];   // comp[n][k]: ways to put n bosons in k modes
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Occupations of basis index r (descending lexicographic order), packed 4 bits per mode.
+__device__ unsigned long long bose_unrank(const BoseTables& T, int64_t r, int* occ) {
+    int rem = T.N;
+    unsigned long long key = 0;
+    for (int p = 0; p < T.K - 1; ++p) {
+        int a = rem;
+        for (; a > 0; --a) {
+            const unsigned long long cnt = T.comp[rem - a][T.K - 1 - p];
+            if ((unsigned long long)r < cnt) break;
+            r -= (int64_t)cnt;
+        }
+        occ[p] = a;
+        key |= (unsigned long long)a << (4 * p);
+        rem -= a;
+    }
+    occ[T.K - 1] = rem;
+    key |= (unsigned long long)rem << (4 * (T.K - 1));
+    return key;
+}
+
+__global__ void k_bose_insert(BoseTables T, int64_t d, unsigned long long* __restrict__ keys,
+                              int32_t* __restrict__ vals, unsigned long long mask,
+                              int32_t* __restrict__ cnt, int* __restrict__ err) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    int occ[16];
+    const unsigned long long key = bose_unrank(T, r, occ);
+    int nocc = 0;
+    for (int i = 0; i < T.K; ++i) nocc += occ[i] > 0;
+    cnt[r] = 1 + nocc * (T.K - 1);
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long prev = atomicCAS(keys + h, kEmpty, key);
+        if (prev == kEmpty || prev == key) {
+            vals[h] = (int32_t)r;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicExch(err, 1);                             // table full (cannot happen at load <= 1/2)
+}
+
+__device__ __forceinline__ int32_t bose_lookup(const unsigned long long* keys, const int32_t* vals,
+                                               unsigned long long mask, unsigned long long key) {
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long k = keys[h];
+        if (k == key) return vals[h];
+        if (k == kEmpty) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+__global__ void k_bose_fill(BoseTables T, const double* __restrict__ cre,
+                            const double* __restrict__ cim, const double* __restrict__ U,
+                            int64_t d, const unsigned long long* __restrict__ keys,
+                            const int32_t* __restrict__ vals, unsigned long long mask,
+                            const int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                            double2* __restrict__ val, int* __restrict__ err) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    int occ[16];
+    const unsigned long long key = bose_unrank(T, r, occ);
+    const int K = T.K;
+    int32_t cs[kBoseMaxEntries];
+    double2 vs[kBoseMaxEntries];
+    double acc = 0.0;
+    for (int i = 0; i < K; ++i) acc = __dadd_rn(acc, __dmul_rn(U[i], (double)(occ[i] * occ[i])));
+    int n = 0;
+    cs[n] = (int32_t)r;
+    vs[n] = make_double2(acc, 0.0);
+    ++n;
+    for (int i = 0; i < K; ++i) {
+        if (occ[i] == 0) continue;
+        for (int j = 0; j < K; ++j) {
+            if (j == i) continue;
+            // source state n - e_i + e_j; <n| c_ij a_i^+ a_j |src> = c_ij sqrt(n_i) sqrt(n_j + 1)
+            const unsigned long long src = key - (1ull << (4 * i)) + (1ull << (4 * j));
+            const int32_t c = bose_lookup(keys, vals, mask, src);
+            if (c < 0) {
+                atomicExch(err, 2);
+                return;
+            }
+            const double amp = __dmul_rn(sqrt((double)occ[i]), sqrt((double)(occ[j] + 1)));
+            double re, im;
+            if (i < j) {
+                const int p = i * K - i * (i + 1) / 2 + (j - i - 1);
+                re = cre[p];
+                im = cim[p];
+            } else {
+                const int p = j * K - j * (j + 1) / 2 + (i - j - 1);
+                re = cre[p];
+                im = -cim[p];
+            }
+            cs[n] = c;
+            vs[n] = make_double2(__dmul_rn(re, amp), __dmul_rn(im, amp));
+            ++n;
+        }
+    }
+    for (int i = 1; i < n; ++i) {
+        const int32_t kc = cs[i];
+        const double2 kv = vs[i];
+        int k = i - 1;
+        while (k >= 0 && cs[k] > kc) {
+            cs[k + 1] = cs[k];
+            vs[k + 1] = vs[k];
+            --k;
+        }
+        cs[k + 1] = kc;
+        vs[k + 1] = kv;
+    }
+    const int64_t p = rowptr[r];
+    if (rowptr[r + 1] - p != n) {
+        atomicExch(err, 3);
+        return;
+    }
+    for (int i = 0; i < n; ++i) {
+        col[p + i] = cs[i];
+        val[p + i] = vs[i];
+    }
+}
+
+// ---------------------------------------------------------------- scan and stats
+
+constexpr int kScanItems = 4;
+constexpr int kScanTile = TE_BLOCK * kScanItems;
+
+__global__ void k_scan_tiles(const int32_t* __restrict__ cnt, int64_t d, int64_t* __restrict__ tile_sum) {
+    __shared__ int64_t sh[TE_BLOCK];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+    for (int q = 0; q < kScanItems; ++q)
+        if (base + q < d) s += cnt[base + q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = TE_BLOCK / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = sh[0];
+}
+
+// Exclusive scan within each tile plus the tile's offset (scanned on the host).
+__global__ void k_scan_apply(const int32_t* __restrict__ cnt, int64_t d,
+                             const int64_t* __restrict__ tile_off, int32_t* __restrict__ rowptr) {
+    __shared__ int64_t sh[TE_BLOCK];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t loc[kScanItems];
+    int64_t s = 0;
+    for (int q = 0; q < kScanItems; ++q) {
+        loc[q] = (base + q < d) ? cnt[base + q] : 0;
+        s += loc[q];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < TE_BLOCK; o <<= 1) {          // Hillis-Steele inclusive scan
+        const int64_t v = (threadIdx.x >= (unsigned)o) ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = tile_off[blockIdx.x] + sh[threadIdx.x] - s;
+    for (int q = 0; q < kScanItems; ++q) {
+        if (base + q < d) rowptr[base + q] = (int32_t)run;
+        run += loc[q];
+    }
+}
+
+__global__ void k_row_stats(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double2* __restrict__ val, int64_t d,
+                            unsigned long long* __restrict__ max_sum_bits,
+                            int* __restrict__ max_nnz, int* __restrict__ flags) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    const int b = rowptr[r], e = rowptr[r + 1];
+    double s = 0.0;
+    bool finite = true, inrange = (e >= b);
+    for (int k = b; k < e; ++k) {
+        const double2 v = val[k];
+        finite &= isfinite(v.x) && isfinite(v.y);
+        s += hypot(v.x, v.y);
+        const int c = col[k];
+        inrange &= (c >= 0) && (c < d);
+    }
+    if (!finite) atomicOr(flags, 1);
+    if (!inrange) atomicOr(flags, 2);
+    if (finite) atomicMax(max_sum_bits, (unsigned long long)__double_as_longlong(s));
+    atomicMax(max_nnz, e - b);
+}
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t n) { return cudaMalloc(&p, n * sizeof(T) + 16); }
+};
+
+int grid_for(int64_t n) { return (int)((n + TE_BLOCK - 1) / TE_BLOCK); }
+
+te_status alloc_matrix(te_ctx* ctx, te_matrix* H, int64_t d, int64_t nnz) {
+    if (nnz >= (1ll << 31) || d >= (1ll << 31))
+        return set_error(ctx, TE_ERR_UNSUPPORTED, "matrix too large: nnz and d must stay below 2^31");
+    H->d = d;
+    H->nnz = nnz;
+    if (cudaMalloc(&H->rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess ||
+        cudaMalloc(&H->col, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        cudaMalloc(&H->val, sizeof(double2) * (nnz > 0 ? nnz : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
+    }
+    return TE_OK;
+}
+
+// rowptr from per-row counts; returns the total through *nnz.
+te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowptr, int64_t* nnz,
+                      cudaStream_t s) {
+    const int64_t tiles = (d + kScanTile - 1) / kScanTile;
+    DevBuf<int64_t> tsum;
+    TE_CUDA_TRY(ctx, tsum.alloc(tiles));
+    k_scan_tiles<<<(int)tiles, TE_BLOCK, 0, s>>>(cnt, d, tsum.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<int64_t> h(tiles);
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), tsum.p, sizeof(int64_t) * tiles,
+                                     cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int64_t run = 0;
+    for (int64_t t = 0; t < tiles; ++t) {
+        const int64_t v = h[t];
+        h[t] = run;
+        run += v;
+    }
+    *nnz = run;
+    if (run >= (1ll << 31))
+        return set_error(ctx, TE_ERR_UNSUPPORTED, "matrix too large: nnz must stay below 2^31");
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(tsum.p, h.data(), sizeof(int64_t) * tiles,
+                                     cudaMemcpyHostToDevice, s));
+    k_scan_apply<<<(int)tiles, TE_BLOCK, 0, s>>>(cnt, d, tsum.p, rowptr);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    const int32_t last = (int32_t)run;
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(rowptr + d, &last, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return TE_OK;
+}
+
+template <typename T>
+te_status upload(te_ctx* ctx, DevBuf<T>& buf, const T* host, size_t n, cudaStream_t s) {
+    TE_CUDA_TRY(ctx, buf.alloc(n));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.p, host, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return TE_OK;
+}
+
+void bose_tables(int K, int N, BoseTables* T) {
+    T->K = K;
+    T->N = N;
+    for (int n = 0; n < 16; ++n)
+        for (int k = 0; k < 17; ++k) {
+            // C(n + k - 1, k - 1) for k >= 1; no way to hold n > 0 bosons in 0 modes
+            if (k == 0) {
+                T->comp[n][k] = (n == 0) ? 1 : 0;
+                continue;
+            }
+            unsigned long long c = 1;
+            for (int i = 1; i <= k - 1; ++i) c = c * (unsigned long long)(n + i) / (unsigned long long)i;
+            T->comp[n][k] = c;
+        }
+}
+
+}  // namespace
+
+te_status build_tfim(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
+    const int L = m->L;
+    if (L < 2 || L > 26 || !m->a || !m->b)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "TFIM needs 2 <= L <= 26 and the J, h arrays");
+    cudaStream_t s = ctx->stream;
+    const int64_t d = 1ll << L;
+    te_status st = alloc_matrix(ctx, H, d, d * (L + 1));
+    if (st) return st;
+    DevBuf<double> J, hx;
+    if ((st = upload(ctx, J, m->a, L - 1, s)) || (st = upload(ctx, hx, m->b, L, s))) return st;
+    k_build_tfim<<<grid_for(d), TE_BLOCK, 0, s>>>(L, J.p, hx.p, d, H->rowptr, H->col, H->val);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return TE_OK;
+}
+
+te_status build_xxzdm(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
+    const int L = m->L;
+    const int nb = m->pbc ? L : L - 1;
+    if (L < 2 || L > 30 || (m->pbc && L < 3) || !m->a || !m->b || !m->c)
+        return set_error(ctx, TE_ERR_INVALID_ARG,
+                         "XXZ-DM needs 2 <= L <= 30 (L >= 3 periodic) and the hop/field arrays");
+    cudaStream_t s = ctx->stream;
+    const int64_t d = 1ll << L;
+    if (d >= (1ll << 31)) return set_error(ctx, TE_ERR_UNSUPPORTED, "dimension must stay below 2^31");
+    DevBuf<int32_t> cnt;
+    TE_CUDA_TRY(ctx, cnt.alloc(d));
+    te_status st;
+    DevBuf<double> hre, him, hz;
+    if ((st = upload(ctx, hre, m->a, nb, s)) || (st = upload(ctx, him, m->b, nb, s)) ||
+        (st = upload(ctx, hz, m->c, L, s)))
+        return st;
+    k_count_xxzdm<<<grid_for(d), TE_BLOCK, 0, s>>>(L, nb, d, cnt.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int32_t* rowptr = nullptr;
+    TE_CUDA_TRY(ctx, cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)));
+    int64_t nnz = 0;
+    if ((st = scan_counts(ctx, cnt.p, d, rowptr, &nnz, s))) {
+        cudaFree(rowptr);
+        return st;
+    }
+    H->d = d;
+    H->nnz = nnz;
+    H->rowptr = rowptr;
+    if (cudaMalloc(&H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
+        cudaMalloc(&H->val, sizeof(double2) * nnz) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
+    }
+    k_fill_xxzdm<<<grid_for(d), TE_BLOCK, 0, s>>>(L, nb, m->delta, hre.p, him.p, hz.p, d, rowptr,
+                                                   H->col, H->val);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return TE_OK;
+}
+
+te_status build_bose(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
+    const int K = m->L, N = m->N;
+    if (K < 2 || K > 16 || N < 1 || N > 15 || !m->a || !m->b || !m->c)
+        return set_error(ctx, TE_ERR_INVALID_ARG,
+                         "bosons need 2 <= K <= 16 modes, 1 <= N <= 15 and the c, U arrays");
+    BoseTables T;
+    bose_tables(K, N, &T);
+    const unsigned long long dd = T.comp[N][K];
+    if (dd >= (1ull << 31)) return set_error(ctx, TE_ERR_UNSUPPORTED, "basis too large");
+    const int64_t d = (int64_t)dd;
+    cudaStream_t s = ctx->stream;
+    unsigned long long cap = 1;
+    while (cap < 2ull * dd) cap <<= 1;
+    DevBuf<unsigned long long> keys;
+    DevBuf<int32_t> vals, cnt;
+    DevBuf<int> err;
+    TE_CUDA_TRY(ctx, keys.alloc(cap));
+    TE_CUDA_TRY(ctx, vals.alloc(cap));
+    TE_CUDA_TRY(ctx, cnt.alloc(d));
+    TE_CUDA_TRY(ctx, err.alloc(1));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(keys.p, 0xff, cap * sizeof(unsigned long long), s));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    const int npair = K * (K - 1) / 2;
+    te_status st;
+    DevBuf<double> cre, cim, U;
+    if ((st = upload(ctx, cre, m->a, npair, s)) || (st = upload(ctx, cim, m->b, npair, s)) ||
+        (st = upload(ctx, U, m->c, K, s)))
+        return st;
+    k_bose_insert<<<grid_for(d), TE_BLOCK, 0, s>>>(T, d, keys.p, vals.p, cap - 1, cnt.p, err.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int32_t* rowptr = nullptr;
+    TE_CUDA_TRY(ctx, cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)));
+    int64_t nnz = 0;
+    if ((st = scan_counts(ctx, cnt.p, d, rowptr, &nnz, s))) {
+        cudaFree(rowptr);
+        return st;
+    }
+    H->d = d;
+    H->nnz = nnz;
+    H->rowptr = rowptr;
+    if (cudaMalloc(&H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
+        cudaMalloc(&H->val, sizeof(double2) * nnz) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
+    }
+    k_bose_fill<<<grid_for(d), TE_BLOCK, 0, s>>>(T, cre.p, cim.p, U.p, d, keys.p, vals.p, cap - 1,
+                                                  rowptr, H->col, H->val, err.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int herr = 0;
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (herr) return set_error(ctx, TE_ERR_INTERNAL, "bosonic basis hash table lookup failed");
+    return TE_OK;
+}
+
+te_status finish_matrix_stats(te_ctx* ctx, te_matrix* H) {
+    cudaStream_t s = ctx->stream;
+    DevBuf<unsigned long long> mx;
+    DevBuf<int> mn, fl;
+    TE_CUDA_TRY(ctx, mx.alloc(1));
+    TE_CUDA_TRY(ctx, mn.alloc(1));
+    TE_CUDA_TRY(ctx, fl.alloc(1));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(mn.p, 0, sizeof(int), s));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(fl.p, 0, sizeof(int), s));
+    k_row_stats<<<grid_for(H->d), TE_BLOCK, 0, s>>>(H->rowptr, H->col, H->val, H->d, mx.p, mn.p, fl.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    unsigned long long bits = 0;
+    int maxnnz = 0, flags = 0;
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(&maxnnz, mn.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(&flags, fl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (flags & 1) return set_error(ctx, TE_ERR_NONFINITE, "matrix has NaN or Inf entries");
+    if (flags & 2) return set_error(ctx, TE_ERR_INVALID_ARG, "column index outside [0, d)");
+    double n1;
+    memcpy(&n1, &bits, sizeof(n1));
+    H->norm1 = n1;
+    H->max_row_nnz = maxnnz;
+    H->lanes = spmv_lanes_for(H->d > 0 ? (double)H->nnz / (double)H->d : 0.0);
+    return TE_OK;
+}
+
+int64_t bose_rank_host(int K, int N, const int32_t* occ) {
+    BoseTables T;
+    bose_tables(K, N, &T);
+    int sum = 0;
+    for (int i = 0; i < K; ++i) {
+        if (occ[i] < 0) return -1;
+        sum += occ[i];
+    }
+    if (sum != N) return -1;
+    int64_t idx = 0;
+    int rem = N;
+    for (int p = 0; p < K - 1; ++p) {
+        for (int a = rem; a > occ[p]; --a) idx += (int64_t)T.comp[rem - a][K - 1 - p];
+        rem -= occ[p];
+    }
+    return idx;
+}

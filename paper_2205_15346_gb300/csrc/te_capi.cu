@@ -1,0 +1,884 @@
+// te_capi.cu -- C ABI, solver engine and request scheduler of libte.
+//
+// A solve (te_evolve, Algorithm 1 of arXiv 2205.15346) runs on a Plan: device
+// buffers for the Krylov basis and the solver state plus one CUDA graph that
+// holds a whole restart (m Lanczos steps, the step kernel, the recombination and
+// a copy of the state to pinned host memory).  The host launches that graph
+// once per restart and reads the copied state to decide whether the solve has
+// reached t; nothing else crosses the PCIe/C2C link inside the solve.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <vector>
+
+#include "te_internal.cuh"
+
+namespace {
+
+const char* kVersion = "libte 0.1 (sm_103a, complex128 restarted Lanczos, arXiv 2205.15346)";
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on P_n from the
+// Chebyshev-like guesses cos(pi (i + 3/4) / (n + 1/2)); P_n by its three-term
+// recurrence, P_n' = n (x P_n - P_{n-1}) / (x^2 - 1), w = 2 / ((1 - x^2) P_n'(x)^2).
+void gauss_legendre_nodes(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p1 = z;
+                p0 = 1.0;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void free_plan(Plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    if (p->V) cudaFree(p->V);
+    if (p->st) cudaFree(p->st);
+    if (p->partials) cudaFree(p->partials);
+    if (p->partials_r) cudaFree(p->partials_r);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->st_init) cudaFreeHost(p->st_init);
+    delete p;
+}
+
+size_t plan_bytes(int64_t d, int m, int reorth, int max_grid) {
+    size_t b = sizeof(double2) * (size_t)(m + 1) * (size_t)d + sizeof(DevState) +
+               sizeof(double) * (size_t)max_grid;
+    if (reorth) b += sizeof(double) * (size_t)max_grid * TE_M_MAX * 2;
+    return b;
+}
+
+// Record one restart of the solve into a graph (see the file comment).
+te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
+    const te_matrix* H = p->H;
+    const int64_t d = p->d;
+    const int m = p->m;
+    TE_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+        const double2* x = p->V + (size_t)j * d;
+        const double2* xprev = j > 0 ? p->V + (size_t)(j - 1) * d : nullptr;
+        double2* y = p->V + (size_t)(j + 1) * d;
+        if (p->profile) e = cudaEventRecord(p->ev[2 * j], s);
+        if (e == cudaSuccess)
+            e = launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
+                                    p->grid_k1, s);
+        if (p->profile && e == cudaSuccess) e = cudaEventRecord(p->ev[2 * j + 1], s);
+        if (e != cudaSuccess) break;
+        if (p->reorth) {
+            e = launch_orth_norm(y, x, d, p->st, j, 1, 0, p->partials, p->grid_stream, s);
+            for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+                e = launch_reorth_dots(p->V, y, d, p->st, j, p->partials_r, p->grid_reorth, s);
+                if (e == cudaSuccess)
+                    e = launch_reorth_update(p->V, y, d, p->st, j, pass == 1, p->partials,
+                                             p->grid_stream, s);
+            }
+        } else {
+            e = launch_orth_norm(y, x, d, p->st, j, j + 1 < m, 1, p->partials, p->grid_stream, s);
+        }
+    }
+    if (e == cudaSuccess) e = launch_step(p->st, m, s);
+    if (e == cudaSuccess) e = launch_recombine(p->V, d, p->st, p->partials, p->grid_stream, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "capturing the restart graph");
+    }
+    if (e2 != cudaSuccess) return cuda_error(ctx, e2, "cudaStreamEndCapture");
+    p->graph = g;
+    TE_CUDA_TRY(ctx, cudaGraphInstantiate(&p->exec, g, 0));
+    return TE_OK;
+}
+
+te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
+                      cudaStream_t s, Plan** out) {
+    Plan* p = new Plan();
+    p->H = H;
+    p->matrix_id = H->id;
+    p->m = m;
+    p->reorth = reorth;
+    p->profile = profile;
+    p->lanes = lanes;
+    p->d = H->d;
+    p->grid_k1 = spmv_grid(lanes, H->d, ctx->num_sms);
+    const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
+    p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
+    p->grid_reorth = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 2);
+    const int max_grid = std::max(p->grid_k1, p->grid_stream);
+    p->bytes = plan_bytes(H->d, m, reorth, max_grid);
+    cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
+    if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * (size_t)max_grid);
+    if (e == cudaSuccess && reorth)
+        e = cudaMalloc(&p->partials_r, sizeof(double) * (size_t)p->grid_reorth * TE_M_MAX * 2);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return set_error(ctx, e == cudaErrorMemoryAllocation ? TE_ERR_OOM : TE_ERR_CUDA,
+                         std::string("allocating the solver workspace: ") + cudaGetErrorString(e));
+    }
+    memset(p->st_host, 0, sizeof(DevState));
+    if (cudaMemsetAsync(p->st, 0, sizeof(DevState), s) != cudaSuccess ||
+        step_prepare(m) != cudaSuccess) {
+        free_plan(p);
+        return set_error(ctx, TE_ERR_CUDA, "preparing the solver workspace");
+    }
+    if (profile) {
+        p->ev.resize(2 * (size_t)m);
+        for (auto& ev : p->ev) cudaEventCreate(&ev);
+    }
+    te_status st = capture_restart(ctx, p, s);
+    if (st) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return TE_OK;
+}
+
+// Take a cached idle plan that fits, or build one (dropping idle plans if the
+// device runs out of memory).
+te_status acquire_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
+                       cudaStream_t s, Plan** out) {
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (Plan* p : ctx->plans)
+            if (!p->in_use && p->matrix_id == H->id && p->m == m && p->reorth == reorth &&
+                p->profile == profile && p->lanes == lanes) {
+                p->in_use = true;
+                *out = p;
+                return TE_OK;
+            }
+    }
+    Plan* p = nullptr;
+    te_status st = create_plan(ctx, H, m, reorth, profile, lanes, s, &p);
+    if (st == TE_ERR_OOM) {
+        std::vector<Plan*> idle;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            auto it = std::partition(ctx->plans.begin(), ctx->plans.end(),
+                                     [](Plan* q) { return q->in_use; });
+            idle.assign(it, ctx->plans.end());
+            ctx->plans.erase(it, ctx->plans.end());
+        }
+        cudaStreamSynchronize(s);
+        for (Plan* q : idle) free_plan(q);
+        st = create_plan(ctx, H, m, reorth, profile, lanes, s, &p);
+    }
+    if (st) return st;
+    p->in_use = true;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->plans.push_back(p);
+    *out = p;
+    return TE_OK;
+}
+
+void release_plan(te_ctx* ctx, Plan* p) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    p->in_use = false;
+}
+
+te_status check_solve_args(te_ctx* ctx, const te_matrix* H, double t, double tol, int32_t m,
+                           const te_options& o) {
+    if (!H) return set_error(ctx, TE_ERR_INVALID_ARG, "H is NULL");
+    if (!(tol > 0.0) || !isfinite(tol)) return set_error(ctx, TE_ERR_INVALID_ARG, "tol must be > 0");
+    if (!isfinite(t)) return set_error(ctx, TE_ERR_INVALID_ARG, "t must be finite");
+    if (m < 1) return set_error(ctx, TE_ERR_INVALID_ARG, "m must be >= 1");
+    if (m > TE_M_MAX) return set_error(ctx, TE_ERR_UNSUPPORTED, "m above TE_M_MAX");
+    if (o.quad != TE_QUAD_TANH_SINH && o.quad != TE_QUAD_GAUSS)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "unknown quadrature");
+    if (o.gauss_n < 2 || o.gauss_n > TE_GAUSS_MAX)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "gauss_n outside 2..64");
+    if (o.n_substeps < 1 || o.max_substeps < 0)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "n_substeps >= 1 and max_substeps >= 0");
+    if (o.reorth != TE_REORTH_NONE && o.reorth != TE_REORTH_FULL)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "unknown reorth mode");
+    if (!(o.t_step0 > 0.0) || !(o.shrink > 0.0 && o.shrink <= 1.0) || !(o.quad_rel_tol > 0.0) ||
+        o.quad_max_levels < 3 || o.quad_max_levels > 20 || !(o.min_step_rel > 0.0))
+        return set_error(ctx, TE_ERR_INVALID_ARG, "step or quadrature option out of range");
+    if (o.spmv_lanes != 0 && (o.spmv_lanes < 1 || o.spmv_lanes > 32 ||
+                              (o.spmv_lanes & (o.spmv_lanes - 1)) != 0))
+        return set_error(ctx, TE_ERR_INVALID_ARG, "spmv_lanes must be 0 or a power of 2 <= 32");
+    return TE_OK;
+}
+
+// One solve on a plan, on stream s.  v_in / v_out: device or host pointers per
+// `dev`.  cancel may be null.
+te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, const double* v_in,
+                    double t, double tol, const te_options& o, double* v_out, bool dev,
+                    te_stats* stats, const std::atomic<int>* cancel) {
+    const double t0 = now_ms();
+    const int64_t d = H->d;
+    DevState* ini = p->st_init;
+    memset(ini, 0, sizeof(DevState));
+    ini->T = fabs(t);
+    ini->tol_rate = (t != 0.0) ? tol / fabs(t) : tol;
+    ini->sign = (t >= 0.0) ? 1.0 : -1.0;
+    ini->t_step0 = o.t_step0;
+    ini->shrink = o.shrink;
+    ini->quad_rel_tol = o.quad_rel_tol;
+    ini->min_step = o.min_step_rel * fabs(t);
+    ini->m = p->m;
+    ini->n_substeps = o.n_substeps;
+    ini->quad = o.quad;
+    ini->gauss_n = o.gauss_n;
+    ini->quad_max_levels = o.quad_max_levels;
+    ini->max_substeps = o.max_substeps;
+    ini->first = 1;
+    ini->m_eff = p->m;
+    gauss_legendre_nodes(o.gauss_n, ini->gx, ini->gw);
+    const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->st, ini, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->V, v_in, sizeof(double2) * d, kin, s));
+    TE_CUDA_TRY(ctx, launch_init_norm(p->V, d, p->st, p->partials, p->grid_stream, s));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const DevState* h = p->st_host;
+    te_stats S;
+    memset(&S, 0, sizeof(S));
+    S.norm_in = h->beta0;
+    S.m_used = p->m;
+    S.roundoff_est = (double)d * H->norm1 * 2.220446049250313e-16;
+    if (S.roundoff_est > tol) S.flags |= TE_WARN_ROUNDOFF;
+    te_status result = TE_OK;
+    if (h->status != 0) {
+        result = h->status;
+        set_error(ctx, result, result == TE_ERR_NONFINITE ? "v_in has NaN or Inf entries"
+                                                         : "v_in is not normalised (| ||v|| - 1 | > 1e-10)");
+    } else if (t != 0.0) {
+        for (;;) {
+            if (cancel && cancel->load()) {
+                result = set_error(ctx, TE_ERR_CANCELLED, "request cancelled");
+                break;
+            }
+            TE_CUDA_TRY(ctx, cudaGraphLaunch(p->exec, s));
+            TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            if (p->profile) {
+                const int me = h->last_m_eff;
+                for (int j = 0; j < me; ++j) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, p->ev[2 * j], p->ev[2 * j + 1]) == cudaSuccess) {
+                        S.spmv_ms += ms;
+                        S.spmv_launches += 1;
+                    }
+                }
+            }
+            if (h->status != 0) {
+                result = h->status;
+                set_error(ctx, result, result == TE_ERR_STEP_UNDERFLOW
+                                           ? "step size underflow: no step meets the error rate"
+                                           : "solver failed on the device");
+                break;
+            }
+            if (h->done) break;
+        }
+    }
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(v_out, p->V, sizeof(double2) * d, kout, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    S.restarts = h->restarts;
+    S.matvecs = h->matvecs;
+    S.breakdowns = h->breakdowns;
+    S.quad_warnings = h->quad_warnings;
+    S.err_bound = h->err_acc;
+    S.t_reached = (t >= 0.0 ? 1.0 : -1.0) * h->t_now;
+    if (h->breakdowns) S.flags |= TE_FLAG_BREAKDOWN;
+    if (h->quad_warnings) S.flags |= TE_WARN_QUAD;
+    if (t == 0.0 && result == TE_OK) S.t_reached = 0.0;
+    S.solve_ms = now_ms() - t0;
+    if (stats) *stats = S;
+    return result;
+}
+
+te_status resolve_options(const te_options* opt, te_options* o) {
+    if (opt) *o = *opt;
+    else te_default_options(o);
+    return TE_OK;
+}
+
+void worker_loop(te_ctx* ctx);
+
+// Order the context's stream after everything already queued on the caller's
+// stream (the caller's buffers may still be in production there).
+te_status join_user_stream(te_ctx* ctx) {
+    TE_CUDA_TRY(ctx, cudaEventRecord(ctx->user_ev, ctx->user_stream));
+    TE_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->user_ev, 0));
+    return TE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ errors
+
+te_status set_error(te_ctx* ctx, te_status s, const std::string& msg) {
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->err = msg;
+    }
+    return s;
+}
+
+te_status cuda_error(te_ctx* ctx, cudaError_t e, const char* what) {
+    const te_status s = (e == cudaErrorMemoryAllocation) ? TE_ERR_OOM : TE_ERR_CUDA;
+    cudaGetLastError();
+    return set_error(ctx, s, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                 cudaGetErrorString(e) + ")");
+}
+
+extern "C" {
+
+const char* te_version(void) { return kVersion; }
+
+const char* te_status_string(te_status s) {
+    switch (s) {
+        case TE_OK: return "TE_OK";
+        case TE_PENDING: return "TE_PENDING";
+        case TE_ERR_INVALID_ARG: return "TE_ERR_INVALID_ARG";
+        case TE_ERR_CUDA: return "TE_ERR_CUDA";
+        case TE_ERR_OOM: return "TE_ERR_OOM";
+        case TE_ERR_NOT_HERMITIAN: return "TE_ERR_NOT_HERMITIAN";
+        case TE_ERR_NOT_NORMALIZED: return "TE_ERR_NOT_NORMALIZED";
+        case TE_ERR_STEP_UNDERFLOW: return "TE_ERR_STEP_UNDERFLOW";
+        case TE_ERR_NONFINITE: return "TE_ERR_NONFINITE";
+        case TE_ERR_TIMEOUT: return "TE_ERR_TIMEOUT";
+        case TE_ERR_CANCELLED: return "TE_ERR_CANCELLED";
+        case TE_ERR_UNSUPPORTED: return "TE_ERR_UNSUPPORTED";
+        case TE_ERR_INTERNAL: return "TE_ERR_INTERNAL";
+        default: return "TE_ERR_UNKNOWN";
+    }
+}
+
+void te_default_options(te_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->quad = TE_QUAD_TANH_SINH;
+    o->gauss_n = 20;
+    o->n_substeps = 10;
+    o->reorth = TE_REORTH_NONE;
+    o->t_step0 = 0.1;
+    o->shrink = 0.97;
+    o->quad_rel_tol = 1e-3;
+    o->quad_max_levels = 15;
+    o->max_substeps = 1000;
+    o->min_step_rel = 1e-13;
+    o->flags = 0;
+    o->spmv_lanes = 0;
+}
+
+const char* te_last_error(const te_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
+    if (!out) return TE_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return TE_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return TE_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return TE_ERR_CUDA;
+    te_ctx* c = new te_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    // Work runs on the context's own non-blocking stream (CUDA graphs cannot be
+    // captured on the legacy default stream); every call first waits for the
+    // caller's stream and returns only after its own work has finished.
+    c->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaEventCreateWithFlags(&c->user_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return TE_ERR_CUDA;
+    }
+    c->own_stream = true;
+    if (cudaMalloc(&c->spmv_st, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost(&c->spmv_st_host, sizeof(DevState)) != cudaSuccess ||
+        cudaMalloc(&c->spmv_partials, sizeof(double) * (size_t)c->num_sms * 64) != cudaSuccess) {
+        te_destroy(c);
+        return TE_ERR_OOM;
+    }
+    cudaMemset(c->spmv_st, 0, sizeof(DevState));
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    c->budget = (int64_t)(0.8 * (double)free_b);
+    *out = c;
+    return TE_OK;
+}
+
+void te_destroy(te_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        ctx->stopping = true;
+        for (te_request* r : ctx->queue) r->cancel.store(1);
+    }
+    ctx->qcv.notify_all();
+    for (auto& t : ctx->workers)
+        if (t.joinable()) t.join();
+    for (Plan* p : ctx->plans) free_plan(p);
+    ctx->plans.clear();
+    if (ctx->spmv_st) cudaFree(ctx->spmv_st);
+    if (ctx->spmv_st_host) cudaFreeHost(ctx->spmv_st_host);
+    if (ctx->spmv_partials) cudaFree(ctx->spmv_partials);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->user_ev) cudaEventDestroy(ctx->user_ev);
+    delete ctx;
+}
+
+// ------------------------------------------------------------------ matrices
+
+te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t* rows,
+                       const int64_t* cols, const double* vals, uint32_t flags, te_matrix** out) {
+    if (!ctx || !out) return TE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d < 1) return set_error(ctx, TE_ERR_INVALID_ARG, "d must be >= 1");
+    if (n_entries < 0) return set_error(ctx, TE_ERR_INVALID_ARG, "n_entries must be >= 0");
+    if (d >= (1ll << 31) || n_entries >= (1ll << 31))
+        return set_error(ctx, TE_ERR_UNSUPPORTED, "d and nnz must stay below 2^31");
+    if (n_entries > 0 && (!rows || !cols || !vals))
+        return set_error(ctx, TE_ERR_INVALID_ARG, "NULL input array");
+    if ((flags & TE_INPUT_IS_CSR) && !rows) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL rowptr");
+    cudaSetDevice(ctx->device);
+    if (te_status js = join_user_stream(ctx)) return js;
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaStream_t s = ctx->stream;
+    const bool csr_in = (flags & TE_INPUT_IS_CSR) != 0;
+    const size_t nrow_in = csr_in ? (size_t)d + 1 : (size_t)n_entries;
+    std::vector<int64_t> R(nrow_in), C(n_entries);
+    std::vector<double> Vv(2 * (size_t)n_entries);
+    const cudaMemcpyKind k = (flags & TE_PTR_DEVICE) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    if (nrow_in) TE_CUDA_TRY(ctx, cudaMemcpy(R.data(), rows, sizeof(int64_t) * nrow_in, k));
+    if (n_entries) {
+        TE_CUDA_TRY(ctx, cudaMemcpy(C.data(), cols, sizeof(int64_t) * n_entries, k));
+        TE_CUDA_TRY(ctx, cudaMemcpy(Vv.data(), vals, sizeof(double) * 2 * n_entries, k));
+    }
+    std::vector<int64_t> rowof(n_entries);
+    if (csr_in) {
+        if (R[0] != 0 || R[d] != n_entries)
+            return set_error(ctx, TE_ERR_INVALID_ARG, "row pointer must start at 0 and end at n_entries");
+        for (int64_t r = 0; r < d; ++r) {
+            if (R[r + 1] < R[r]) return set_error(ctx, TE_ERR_INVALID_ARG, "row pointer not monotone");
+            for (int64_t q = R[r]; q < R[r + 1]; ++q) rowof[q] = r;
+        }
+    } else {
+        for (int64_t q = 0; q < n_entries; ++q) rowof[q] = R[q];
+    }
+    for (int64_t q = 0; q < n_entries; ++q) {
+        if (rowof[q] < 0 || rowof[q] >= d || C[q] < 0 || C[q] >= d)
+            return set_error(ctx, TE_ERR_INVALID_ARG, "entry index outside [0, d)");
+        if (!isfinite(Vv[2 * q]) || !isfinite(Vv[2 * q + 1]))
+            return set_error(ctx, TE_ERR_NONFINITE, "NaN or Inf value");
+    }
+    std::vector<int64_t> ord(n_entries);
+    for (int64_t q = 0; q < n_entries; ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        return rowof[a] != rowof[b] ? rowof[a] < rowof[b] : C[a] < C[b];
+    });
+    std::vector<int32_t> rp(d + 1, 0), cc;
+    std::vector<double> vv;
+    cc.reserve(n_entries);
+    vv.reserve(2 * n_entries);
+    int64_t prev_r = -1, prev_c = -1;
+    for (int64_t q : ord) {
+        const int64_t r = rowof[q], c = C[q];
+        if (r == prev_r && c == prev_c) {
+            vv[vv.size() - 2] += Vv[2 * q];
+            vv[vv.size() - 1] += Vv[2 * q + 1];
+        } else {
+            cc.push_back((int32_t)c);
+            vv.push_back(Vv[2 * q]);
+            vv.push_back(Vv[2 * q + 1]);
+            rp[r + 1] += 1;
+            prev_r = r;
+            prev_c = c;
+        }
+    }
+    for (int64_t r = 0; r < d; ++r) rp[r + 1] += rp[r];
+    const int64_t nnz = (int64_t)cc.size();
+    if (flags & TE_CHECK_HERMITIAN) {
+        double mx = 0.0;
+        for (int64_t q = 0; q < nnz; ++q) mx = std::max(mx, hypot(vv[2 * q], vv[2 * q + 1]));
+        const double tolh = 1e-13 * mx;
+        for (int64_t r = 0; r < d; ++r)
+            for (int32_t q = rp[r]; q < rp[r + 1]; ++q) {
+                const int64_t c = cc[q];
+                auto b = cc.begin() + rp[c], e = cc.begin() + rp[c + 1];
+                auto it = std::lower_bound(b, e, (int32_t)r);
+                double tre = 0.0, tim = 0.0;
+                if (it != e && *it == r) {
+                    const size_t w = (size_t)(it - cc.begin());
+                    tre = vv[2 * w];
+                    tim = vv[2 * w + 1];
+                }
+                if (fabs(vv[2 * q] - tre) > tolh || fabs(vv[2 * q + 1] + tim) > tolh)
+                    return set_error(ctx, TE_ERR_NOT_HERMITIAN, "H[i,j] != conj(H[j,i])");
+            }
+    }
+    te_matrix* H = new te_matrix();
+    H->ctx = ctx;
+    H->d = d;
+    H->nnz = nnz;
+    if (cudaMalloc(&H->rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess ||
+        cudaMalloc(&H->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+        cudaMalloc(&H->val, sizeof(double2) * std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        te_matrix_free(H);
+        return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
+    }
+    cudaMemcpyAsync(H->rowptr, rp.data(), sizeof(int32_t) * (d + 1), cudaMemcpyHostToDevice, s);
+    if (nnz) {
+        cudaMemcpyAsync(H->col, cc.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(H->val, vv.data(), sizeof(double2) * nnz, cudaMemcpyHostToDevice, s);
+    }
+    te_status st = finish_matrix_stats(ctx, H);
+    if (st) {
+        te_matrix_free(H);
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        H->id = ctx->next_matrix_id++;
+    }
+    *out = H;
+    return TE_OK;
+}
+
+te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out) {
+    if (!ctx || !desc || !out) return TE_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    te_matrix* H = new te_matrix();
+    H->ctx = ctx;
+    te_status st;
+    switch (desc->model) {
+        case TE_MODEL_TFIM: st = build_tfim(ctx, desc, H); break;
+        case TE_MODEL_XXZDM: st = build_xxzdm(ctx, desc, H); break;
+        case TE_MODEL_BOSE: st = build_bose(ctx, desc, H); break;
+        default: st = set_error(ctx, TE_ERR_INVALID_ARG, "unknown model");
+    }
+    if (st == TE_OK) st = finish_matrix_stats(ctx, H);
+    if (st) {
+        te_matrix_free(H);
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        H->id = ctx->next_matrix_id++;
+    }
+    *out = H;
+    return TE_OK;
+}
+
+te_status te_model_basis_index(const te_model_desc* desc, const int32_t* occ, int64_t* index) {
+    if (!desc || !occ || !index) return TE_ERR_INVALID_ARG;
+    if (desc->model != TE_MODEL_BOSE || desc->L < 2 || desc->L > 16 || desc->N < 1 || desc->N > 15)
+        return TE_ERR_INVALID_ARG;
+    const int64_t r = bose_rank_host(desc->L, desc->N, occ);
+    if (r < 0) return TE_ERR_INVALID_ARG;
+    *index = r;
+    return TE_OK;
+}
+
+te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
+    if (!H || !info) return TE_ERR_INVALID_ARG;
+    info->d = H->d;
+    info->nnz = H->nnz;
+    info->norm1 = H->norm1;
+    info->max_row_nnz = H->max_row_nnz;
+    info->spmv_lanes = H->lanes;
+    return TE_OK;
+}
+
+te_status te_matrix_export(te_ctx* ctx, const te_matrix* H, int32_t* rowptr, int32_t* col,
+                           double* val, uint32_t flags) {
+    if (!ctx || !H) return TE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    if (te_status js = join_user_stream(ctx)) return js;
+    const cudaMemcpyKind k = (flags & TE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t s = ctx->stream;
+    if (rowptr) TE_CUDA_TRY(ctx, cudaMemcpyAsync(rowptr, H->rowptr, sizeof(int32_t) * (H->d + 1), k, s));
+    if (col && H->nnz) TE_CUDA_TRY(ctx, cudaMemcpyAsync(col, H->col, sizeof(int32_t) * H->nnz, k, s));
+    if (val && H->nnz) TE_CUDA_TRY(ctx, cudaMemcpyAsync(val, H->val, sizeof(double2) * H->nnz, k, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return TE_OK;
+}
+
+void te_matrix_free(te_matrix* H) {
+    if (!H) return;
+    te_ctx* ctx = H->ctx;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        std::vector<Plan*> drop;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            auto it = std::partition(ctx->plans.begin(), ctx->plans.end(),
+                                     [&](Plan* p) { return p->matrix_id != H->id || p->in_use; });
+            drop.assign(it, ctx->plans.end());
+            ctx->plans.erase(it, ctx->plans.end());
+        }
+        for (Plan* p : drop) free_plan(p);
+    }
+    if (H->rowptr) cudaFree(H->rowptr);
+    if (H->col) cudaFree(H->col);
+    if (H->val) cudaFree(H->val);
+    delete H;
+}
+
+// ------------------------------------------------------------------ products and solves
+
+te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, double* x_dot_y,
+                  uint32_t flags) {
+    if (!ctx || !H || !x || !y) return TE_ERR_INVALID_ARG;
+    if (x == y) return set_error(ctx, TE_ERR_INVALID_ARG, "x and y must be distinct buffers");
+    cudaSetDevice(ctx->device);
+    if (te_status js = join_user_stream(ctx)) return js;
+    cudaStream_t s = ctx->stream;
+    const bool dev = (flags & TE_PTR_DEVICE) != 0;
+    const int64_t d = H->d;
+    double2 *xd = (double2*)x, *yd = (double2*)y;
+    double2 *xtmp = nullptr, *ytmp = nullptr;
+    if (!dev) {
+        TE_CUDA_TRY(ctx, cudaMalloc(&xtmp, sizeof(double2) * d));
+        if (cudaMalloc(&ytmp, sizeof(double2) * d) != cudaSuccess) {
+            cudaFree(xtmp);
+            return cuda_error(ctx, cudaErrorMemoryAllocation, "te_spmv scratch");
+        }
+        cudaMemcpyAsync(xtmp, x, sizeof(double2) * d, cudaMemcpyHostToDevice, s);
+        xd = xtmp;
+        yd = ytmp;
+    }
+    const int grid = std::min(spmv_grid(H->lanes, d, ctx->num_sms), ctx->num_sms * 64);
+    cudaError_t e = launch_spmv_lanczos(H, H->lanes, xd, nullptr, yd, ctx->spmv_st, 0, 1,
+                                        ctx->spmv_partials, grid, s);
+    if (e == cudaSuccess && !dev)
+        e = cudaMemcpyAsync(y, yd, sizeof(double2) * d, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->spmv_st_host, ctx->spmv_st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (xtmp) cudaFree(xtmp);
+    if (ytmp) cudaFree(ytmp);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "te_spmv");
+    if (x_dot_y) *x_dot_y = ctx->spmv_st_host->spmv_dot;
+    return TE_OK;
+}
+
+te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
+                    int32_t m, const te_options* opt, double* v_out, te_stats* st) {
+    if (!ctx) return TE_ERR_INVALID_ARG;
+    if (!v_in || !v_out) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL vector");
+    te_options o;
+    resolve_options(opt, &o);
+    te_status s = check_solve_args(ctx, H, t, tol, m, o);
+    if (s) return s;
+    cudaSetDevice(ctx->device);
+    if ((s = join_user_stream(ctx))) return s;
+    const int mu = (int)std::min<int64_t>(m, H->d);
+    const int lanes = o.spmv_lanes ? o.spmv_lanes : H->lanes;
+    Plan* p = nullptr;
+    s = acquire_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, lanes, ctx->stream, &p);
+    if (s) return s;
+    s = run_solve(ctx, H, p, ctx->stream, v_in, t, tol, o, v_out, (o.flags & TE_PTR_DEVICE) != 0,
+                  st, nullptr);
+    release_plan(ctx, p);
+    return s;
+}
+
+// ------------------------------------------------------------------ requests
+
+te_status te_set_memory_budget(te_ctx* ctx, int64_t bytes) {
+    if (!ctx || bytes <= 0) return TE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->qmu);
+    ctx->budget = bytes;
+    ctx->qcv.notify_all();
+    return TE_OK;
+}
+
+te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
+                    int32_t m, const te_options* opt, te_request** out) {
+    if (!ctx || !out) return TE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!v_in) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL vector");
+    te_options o;
+    resolve_options(opt, &o);
+    te_status s = check_solve_args(ctx, H, t, tol, m, o);
+    if (s) return s;
+    cudaSetDevice(ctx->device);
+    if ((s = join_user_stream(ctx))) return s;
+    te_request* r = new te_request();
+    r->ctx = ctx;
+    r->H = H;
+    r->t = t;
+    r->tol = tol;
+    r->m = (int32_t)std::min<int64_t>(m, H->d);
+    r->opt = o;
+    const size_t vb = sizeof(double2) * (size_t)H->d;
+    if (cudaMalloc(&r->v_in_dev, vb) != cudaSuccess || cudaMalloc(&r->v_out_dev, vb) != cudaSuccess) {
+        cudaGetLastError();
+        te_request_free(r);
+        return set_error(ctx, TE_ERR_OOM, "request vectors");
+    }
+    const cudaMemcpyKind k = (o.flags & TE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(r->v_in_dev, v_in, vb, k, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        te_request_free(r);
+        return cuda_error(ctx, cudaGetLastError(), "copying the request vector");
+    }
+    r->footprint = plan_bytes(H->d, r->m, o.reorth, ctx->num_sms * 8);
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        ctx->queue.push_back(r);
+        if ((int)ctx->workers.size() < ctx->max_workers) ctx->workers.emplace_back(worker_loop, ctx);
+    }
+    ctx->qcv.notify_all();
+    *out = r;
+    return TE_OK;
+}
+
+te_status te_poll(te_request* r, double* v_out, te_stats* st) {
+    if (!r) return TE_ERR_INVALID_ARG;
+    if (r->state.load() != 2) return TE_PENDING;
+    if (v_out) {
+        cudaSetDevice(r->ctx->device);
+        const cudaMemcpyKind k = (r->opt.flags & TE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                : cudaMemcpyDeviceToHost;
+        if (cudaMemcpy(v_out, r->v_out_dev, sizeof(double2) * (size_t)r->H->d, k) != cudaSuccess)
+            return cuda_error(r->ctx, cudaGetLastError(), "te_poll copy");
+    }
+    if (st) *st = r->stats;
+    return r->result;
+}
+
+te_status te_wait(te_request* r, double timeout_ms, double* v_out, te_stats* st) {
+    if (!r) return TE_ERR_INVALID_ARG;
+    {
+        std::unique_lock<std::mutex> lk(r->mu);
+        auto pred = [&] { return r->state.load() == 2; };
+        if (timeout_ms < 0) r->cv.wait(lk, pred);
+        else r->cv.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred);
+    }
+    return te_poll(r, v_out, st);
+}
+
+te_status te_cancel(te_request* r) {
+    if (!r) return TE_ERR_INVALID_ARG;
+    r->cancel.store(1);
+    return TE_OK;
+}
+
+void te_request_free(te_request* r) {
+    if (!r) return;
+    te_ctx* ctx = r->ctx;
+    bool queued_removed = false;
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        auto it = std::find(ctx->queue.begin(), ctx->queue.end(), r);
+        if (it != ctx->queue.end()) {
+            ctx->queue.erase(it);
+            queued_removed = true;
+        }
+    }
+    if (!queued_removed && r->state.load() == 1) {
+        std::unique_lock<std::mutex> lk(r->mu);
+        r->cv.wait(lk, [&] { return r->state.load() == 2; });
+    }
+    if (ctx) cudaSetDevice(ctx->device);
+    if (r->v_in_dev) cudaFree(r->v_in_dev);
+    if (r->v_out_dev) cudaFree(r->v_out_dev);
+    delete r;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Scheduler worker: admits the oldest queued request once its footprint fits the
+// budget (or nothing else is running), runs it on the worker's own stream one
+// restart at a time, and publishes the result.
+void worker_loop(te_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (;;) {
+        te_request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->qcv.wait(lk, [&] {
+                if (ctx->stopping) return true;
+                if (ctx->queue.empty()) return false;
+                te_request* f = ctx->queue.front();
+                return ctx->in_use == 0 || ctx->in_use + (int64_t)f->footprint <= ctx->budget;
+            });
+            if (ctx->stopping && ctx->queue.empty()) break;
+            if (ctx->stopping) {
+                r = ctx->queue.front();
+                ctx->queue.pop_front();
+                r->cancel.store(1);
+            } else {
+                r = ctx->queue.front();
+                ctx->queue.pop_front();
+                ctx->in_use += (int64_t)r->footprint;
+            }
+            r->state.store(1);
+        }
+        te_status res;
+        te_stats S;
+        memset(&S, 0, sizeof(S));
+        if (r->cancel.load()) {
+            res = TE_ERR_CANCELLED;
+        } else {
+            Plan* p = nullptr;
+            const int lanes = r->opt.spmv_lanes ? r->opt.spmv_lanes : r->H->lanes;
+            res = acquire_plan(ctx, r->H, r->m, r->opt.reorth,
+                               (r->opt.flags & TE_OPT_PROFILE) ? 1 : 0, lanes, s, &p);
+            if (res == TE_OK) {
+                res = run_solve(ctx, r->H, p, s, r->v_in_dev, r->t, r->tol, r->opt, r->v_out_dev,
+                                true, &S, &r->cancel);
+                release_plan(ctx, p);
+            }
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            ctx->in_use -= (int64_t)r->footprint;
+        }
+        ctx->qcv.notify_all();
+        {
+            std::lock_guard<std::mutex> lk(r->mu);
+            r->stats = S;
+            r->result = res;
+            r->state.store(2);
+        }
+        r->cv.notify_all();
+    }
+    if (s) cudaStreamDestroy(s);
+}
+
+}  // namespace

@@ -1,0 +1,199 @@
+// te_internal.cuh -- shared declarations of libte's translation units.
+//
+// Device-side solver state, matrix and plan objects, and the host launchers of
+// the kernels.  Kernel numbering follows the restart cycle of Algorithm 1 of
+// arXiv 2205.15346:
+//   K0  k_init_norm      ||v_in||, validation (Sec. 2.1 assumes ||v(0)|| = 1)
+//   K1  k_spmv_lanczos   y = s H u_j - beta_{j-1} v_{j-1}, partial Re<v_j, y>   (eq. arnoldi a-c)
+//   K2  k_orth_norm      w~ = y - alpha_j v_j, ||w~||, breakdown test          (eq. arnoldi d-f)
+//   KR  k_reorth_*       optional full Gram-Schmidt (not in the paper)
+//   K3  k_step           eigen-decomposition of H_m, error integral, step size, omega
+//                         (Sec. 2.4 step 2, eqs. errorIntegral, errorRate, stepSize)
+//   K4  k_recombine      w = V_m omega, ||w||                                   (Algorithm 1 step 3)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "te.h"
+
+#define TE_BLOCK 256                 // threads per block of the streaming kernels
+#define TE_STEP_THREADS 256          // threads of the single-CTA step kernel
+#define TE_GAUSS_MAX 64
+
+// Solver state in device memory, one per plan.  Written by the kernels of a
+// restart, read back by the host after each restart (a copy of the struct).
+struct DevState {
+    // constants of a solve (set by the host before the first restart)
+    double T;                // |t|
+    double tol_rate;         // err_max / |t|  (eq. errorRate)
+    double sign;             // +1: H, -1: -H (negative t)
+    double t_step0;
+    double shrink;
+    double quad_rel_tol;
+    double min_step;         // min_step_rel * |t|
+    int32_t m;               // Krylov dimension (clamped to d)
+    int32_t n_substeps;
+    int32_t quad;
+    int32_t gauss_n;
+    int32_t quad_max_levels;
+    int32_t max_substeps;
+    // progress of the solve
+    double t_now;
+    double prev_step;
+    double err_acc;
+    int32_t first;
+    int32_t done;
+    int32_t status;          // te_status of the solve (0 while fine)
+    int32_t last_m_eff;      // Krylov size used by the last finished restart
+    int64_t restarts;
+    int64_t matvecs;
+    int64_t breakdowns;
+    int64_t quad_warnings;
+    // state of the current restart
+    int32_t stop;            // inner Lanczos loop ended (breakdown)
+    int32_t m_eff;
+    int32_t breakdown;
+    int32_t pad0;
+    double beta0;            // ||w|| at the start of the restart
+    double as_cur;           // alpha_j * scale_j, handed from K1 to K2
+    double spmv_dot;         // te_spmv: Re <x, H x>
+    double last_step;
+    double last_err;
+    double scale[TE_M_MAX + 1];   // v_j = scale[j] * u_j (stored vectors are unnormalised)
+    double alpha[TE_M_MAX];       // diagonal of H_m
+    double beta[TE_M_MAX];        // beta[j] = h_{j+2,j+1} (0-based j); h = beta[m_eff-1]
+    double2 coef[TE_M_MAX];       // recombination coefficients beta0 * scale[k] * omega_k
+    double2 rcoef[TE_M_MAX];      // reorthogonalisation coefficients
+    double gx[TE_GAUSS_MAX];      // Gauss-Legendre nodes on [-1, 1]
+    double gw[TE_GAUSS_MAX];
+    unsigned int counter[8];      // last-block counters of the reductions
+};
+
+struct te_matrix {
+    te_ctx* ctx;
+    int64_t d;
+    int64_t nnz;
+    int32_t* rowptr;         // device, d + 1
+    int32_t* col;            // device, nnz
+    double2* val;            // device, nnz
+    double norm1;
+    int32_t max_row_nnz;
+    int32_t lanes;           // lanes per row for the SpMV
+    uint64_t id;
+};
+
+// One solve's device workspace and captured restart graph.
+struct Plan {
+    const te_matrix* H = nullptr;
+    uint64_t matrix_id = 0;
+    int m = 0;
+    int reorth = 0;
+    int profile = 0;
+    int lanes = 0;
+    int64_t d = 0;
+    double2* V = nullptr;            // (m + 1) columns of length d, column-major
+    DevState* st = nullptr;          // device
+    DevState* st_host = nullptr;     // pinned: written by the graph's last node
+    DevState* st_init = nullptr;     // pinned: source of the per-solve initial state
+    double* partials = nullptr;      // per-block reduction scratch
+    double* partials_r = nullptr;    // reorthogonalisation scratch
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;     // TE_OPT_PROFILE: start/stop per Lanczos step
+    size_t bytes = 0;
+    bool in_use = false;
+    int grid_k1 = 0, grid_stream = 0, grid_reorth = 0;
+};
+
+struct te_ctx;
+
+struct te_request {
+    te_ctx* ctx = nullptr;
+    const te_matrix* H = nullptr;
+    double* v_in_dev = nullptr;      // library-owned copy of v_in
+    double* v_out_dev = nullptr;
+    double t = 0, tol = 0;
+    int32_t m = 0;
+    te_options opt{};
+    te_stats stats{};
+    size_t footprint = 0;
+    std::atomic<int> state{0};       // 0 queued, 1 running, 2 finished
+    std::atomic<int> cancel{0};
+    te_status result = TE_PENDING;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool freed_by_user = false;
+};
+
+struct te_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;        // the context's own non-blocking stream
+    cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy default)
+    cudaEvent_t user_ev = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string err;
+    std::mutex mu;                   // plans, matrices
+    std::vector<Plan*> plans;
+    uint64_t next_matrix_id = 1;
+    // te_spmv scratch
+    DevState* spmv_st = nullptr;
+    DevState* spmv_st_host = nullptr;
+    double* spmv_partials = nullptr;
+    // scheduler
+    std::mutex qmu;
+    std::condition_variable qcv;
+    std::deque<te_request*> queue;
+    std::vector<std::thread> workers;
+    bool stopping = false;
+    int64_t budget = 0;
+    int64_t in_use = 0;
+    int max_workers = 8;
+};
+
+// ---- host launchers (kernels live in te_lanczos.cu, te_step.cu, te_build.cu)
+
+int spmv_lanes_for(double avg_row_nnz);
+cudaError_t launch_init_norm(const double2* v, int64_t d, DevState* st, double* partials,
+                             int grid, cudaStream_t s);
+cudaError_t launch_spmv_lanczos(const te_matrix* H, int lanes, const double2* x,
+                                const double2* xprev, double2* y, DevState* st, int j,
+                                int mode, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_orth_norm(double2* w, const double2* u, int64_t d, DevState* st, int j,
+                             int write, int decide, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_reorth_dots(const double2* V, const double2* w, int64_t d, DevState* st,
+                               int j, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_reorth_update(const double2* V, double2* w, int64_t d, DevState* st, int j,
+                                 int decide, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_step(DevState* st, int m, cudaStream_t s);
+cudaError_t launch_recombine(double2* V, int64_t d, DevState* st, double* partials, int grid,
+                             cudaStream_t s);
+int spmv_grid(int lanes, int64_t d, int num_sms);
+int occupancy_grid_spmv(int lanes, int num_sms);
+int step_smem_bytes(int m);
+cudaError_t step_prepare(int m);
+
+// builders
+te_status build_tfim(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
+te_status build_xxzdm(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
+te_status build_bose(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
+te_status finish_matrix_stats(te_ctx* ctx, te_matrix* H);
+int64_t bose_rank_host(int K, int N, const int32_t* occ);
+
+te_status set_error(te_ctx* ctx, te_status s, const std::string& msg);
+te_status cuda_error(te_ctx* ctx, cudaError_t e, const char* what);
+
+#define TE_CUDA_TRY(ctx, call)                                   \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return cuda_error((ctx), _e, #call); \
+    } while (0)

@@ -1,0 +1,381 @@
+"""Python binding of libte (ctypes): argument marshalling only.
+
+Every function mirrors the C entry point of the same name in ``include/te.h``;
+all arithmetic happens in libte's CUDA kernels.  Vectors are numpy complex128
+arrays (host) or torch complex128 CUDA tensors (device); the binding sets
+TE_PTR_DEVICE accordingly.  Loading fails loudly when libte.so is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libte.so")
+
+TE_OK = 0
+TE_PENDING = 1
+TE_ERR_INVALID_ARG = -1
+TE_ERR_CUDA = -2
+TE_ERR_OOM = -3
+TE_ERR_NOT_HERMITIAN = -4
+TE_ERR_NOT_NORMALIZED = -5
+TE_ERR_STEP_UNDERFLOW = -6
+TE_ERR_NONFINITE = -7
+TE_ERR_TIMEOUT = -8
+TE_ERR_CANCELLED = -9
+TE_ERR_UNSUPPORTED = -10
+TE_ERR_INTERNAL = -11
+
+TE_PTR_DEVICE = 0x1
+TE_CHECK_HERMITIAN = 0x2
+TE_INPUT_IS_CSR = 0x4
+TE_WARN_ROUNDOFF = 0x1
+TE_WARN_QUAD = 0x2
+TE_FLAG_BREAKDOWN = 0x4
+TE_M_MAX = 128
+TE_QUAD_TANH_SINH = 0
+TE_QUAD_GAUSS = 1
+TE_REORTH_NONE = 0
+TE_REORTH_FULL = 1
+TE_OPT_PROFILE = 0x10
+TE_MODEL_TFIM = 1
+TE_MODEL_XXZDM = 2
+TE_MODEL_BOSE = 3
+
+
+class te_options(C.Structure):
+    _fields_ = [("quad", C.c_int32), ("gauss_n", C.c_int32), ("n_substeps", C.c_int32),
+                ("reorth", C.c_int32), ("t_step0", C.c_double), ("shrink", C.c_double),
+                ("quad_rel_tol", C.c_double), ("quad_max_levels", C.c_int32),
+                ("max_substeps", C.c_int32), ("min_step_rel", C.c_double), ("flags", C.c_uint32),
+                ("spmv_lanes", C.c_int32)]
+
+
+class te_stats(C.Structure):
+    _fields_ = [("restarts", C.c_int64), ("matvecs", C.c_int64), ("breakdowns", C.c_int64),
+                ("quad_warnings", C.c_int64), ("err_bound", C.c_double),
+                ("roundoff_est", C.c_double), ("t_reached", C.c_double), ("norm_in", C.c_double),
+                ("flags", C.c_uint32), ("m_used", C.c_int32), ("spmv_ms", C.c_double),
+                ("spmv_launches", C.c_int64), ("solve_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class te_matrix_info(C.Structure):
+    _fields_ = [("d", C.c_int64), ("nnz", C.c_int64), ("norm1", C.c_double),
+                ("max_row_nnz", C.c_int32), ("spmv_lanes", C.c_int32)]
+
+
+class te_model_desc(C.Structure):
+    _fields_ = [("model", C.c_int32), ("L", C.c_int32), ("N", C.c_int32), ("pbc", C.c_int32),
+                ("delta", C.c_double), ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
+                ("c", C.POINTER(C.c_double))]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "te_version": (C.c_char_p, []),
+    "te_status_string": (C.c_char_p, [C.c_int32]),
+    "te_default_options": (None, [C.POINTER(te_options)]),
+    "te_create": (C.c_int32, [C.POINTER(_P), C.c_int32, _P]),
+    "te_destroy": (None, [_P]),
+    "te_last_error": (C.c_char_p, [_P]),
+    "te_build_csr": (C.c_int32, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_uint32, C.POINTER(_P)]),
+    "te_build_model": (C.c_int32, [_P, C.POINTER(te_model_desc), C.POINTER(_P)]),
+    "te_model_basis_index": (C.c_int32, [C.POINTER(te_model_desc), _P, C.POINTER(C.c_int64)]),
+    "te_matrix_info_get": (C.c_int32, [_P, C.POINTER(te_matrix_info)]),
+    "te_matrix_export": (C.c_int32, [_P, _P, _P, _P, _P, C.c_uint32]),
+    "te_matrix_free": (None, [_P]),
+    "te_spmv": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
+    "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
+                              C.POINTER(te_options), _P, C.POINTER(te_stats)]),
+    "te_submit": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
+                              C.POINTER(te_options), C.POINTER(_P)]),
+    "te_poll": (C.c_int32, [_P, _P, C.POINTER(te_stats)]),
+    "te_wait": (C.c_int32, [_P, C.c_double, _P, C.POINTER(te_stats)]),
+    "te_cancel": (C.c_int32, [_P]),
+    "te_request_free": (None, [_P]),
+    "te_set_memory_budget": (C.c_int32, [_P, C.c_int64]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libte.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libte.so not found at {LIB_PATH}; build it first "
+                               "(python -m paper_2205_15346_gb300.build)")
+        handle = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+class TEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{te_status_string(status)}: {msg}")
+        self.status = status
+
+
+def te_status_string(s: int) -> str:
+    return lib().te_status_string(s).decode()
+
+
+def te_version() -> str:
+    return lib().te_version().decode()
+
+
+def _check(ctx, status: int, allow=(TE_OK,)):
+    if status not in allow:
+        msg = lib().te_last_error(ctx).decode() if ctx else ""
+        raise TEError(status, msg)
+    return status
+
+
+# ---------------------------------------------------------------- marshalling helpers
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _vec_ptr(x, d: int, writable: bool = False):
+    """(pointer, is_device, keepalive) for a complex128 vector of length d."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.complex128 or x.numel() != d or not x.is_contiguous():
+            raise ValueError("expected a contiguous complex128 tensor of length d")
+        return C.c_void_p(x.data_ptr()), x.is_cuda, x
+    a = np.asarray(x)
+    if a.dtype != np.complex128 or a.size != d or not a.flags["C_CONTIGUOUS"]:
+        if writable:
+            raise ValueError("output must be a contiguous complex128 array of length d")
+        a = np.ascontiguousarray(a, dtype=np.complex128).reshape(-1)
+        if a.size != d:
+            raise ValueError("vector length does not match d")
+    return C.c_void_p(a.ctypes.data), False, a
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data_as(C.POINTER(C.c_double)), a
+
+
+def te_default_options() -> te_options:
+    o = te_options()
+    lib().te_default_options(C.byref(o))
+    return o
+
+
+def make_options(**kw) -> te_options:
+    o = te_default_options()
+    for k, v in kw.items():
+        if k == "quad" and isinstance(v, str):
+            v = {"tanh-sinh": TE_QUAD_TANH_SINH, "gauss": TE_QUAD_GAUSS}[v]
+        if k == "reorth" and isinstance(v, bool):
+            v = TE_REORTH_FULL if v else TE_REORTH_NONE
+        if k == "profile":
+            o.flags |= TE_OPT_PROFILE if v else 0
+            continue
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------- C entry points
+
+def te_create(device: int = 0, stream=None):
+    """Context on ``device``; ``stream`` is a cudaStream_t handle (int) or None
+    (then torch's current stream on that device, if torch is loaded)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream(device).cuda_stream
+        except Exception:
+            stream = None
+    out = C.c_void_p()
+    s = lib().te_create(C.byref(out), device, C.c_void_p(stream or 0))
+    _check(None, s)
+    return out
+
+
+def te_destroy(ctx) -> None:
+    lib().te_destroy(ctx)
+
+
+def te_last_error(ctx) -> str:
+    return lib().te_last_error(ctx).decode()
+
+
+def model_desc(params: dict):
+    """te_model_desc from a parameter table of the ``workloads`` module (plus keepalives)."""
+    m = params["model"]
+    desc = te_model_desc()
+    keep = []
+    if m == "tfim":
+        desc.model, desc.L = TE_MODEL_TFIM, params["L"]
+        desc.a, k1 = _dptr(params["J"])
+        desc.b, k2 = _dptr(params["h"])
+        keep = [k1, k2]
+    elif m == "xxzdm":
+        desc.model, desc.L = TE_MODEL_XXZDM, params["L"]
+        desc.pbc, desc.delta = int(params["pbc"]), float(params["delta"])
+        desc.a, k1 = _dptr(params["hop_re"])
+        desc.b, k2 = _dptr(params["hop_im"])
+        desc.c, k3 = _dptr(params["hz"])
+        keep = [k1, k2, k3]
+    elif m == "bose":
+        desc.model, desc.L, desc.N = TE_MODEL_BOSE, params["K"], params["N"]
+        desc.a, k1 = _dptr(params["c_re"])
+        desc.b, k2 = _dptr(params["c_im"])
+        desc.c, k3 = _dptr(params["U"])
+        keep = [k1, k2, k3]
+    else:
+        raise ValueError(m)
+    return desc, keep
+
+
+def te_build_model(ctx, params: dict):
+    desc, keep = model_desc(params)
+    out = C.c_void_p()
+    _check(ctx, lib().te_build_model(ctx, C.byref(desc), C.byref(out)))
+    return out
+
+
+def te_model_basis_index(params: dict, occ) -> int:
+    desc, keep = model_desc(params)
+    o = np.ascontiguousarray(occ, dtype=np.int32)
+    idx = C.c_int64()
+    _check(None, lib().te_model_basis_index(C.byref(desc), C.c_void_p(o.ctypes.data), C.byref(idx)))
+    return idx.value
+
+
+def te_build_csr(ctx, d: int, rows, cols, vals, flags: int = 0):
+    """H from COO (or CSR with TE_INPUT_IS_CSR) host arrays; vals complex128."""
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    c = np.ascontiguousarray(cols, dtype=np.int64)
+    v = np.ascontiguousarray(vals, dtype=np.complex128)
+    n = c.size
+    out = C.c_void_p()
+    _check(ctx, lib().te_build_csr(ctx, d, n, C.c_void_p(r.ctypes.data), C.c_void_p(c.ctypes.data),
+                                   C.c_void_p(v.ctypes.data), flags, C.byref(out)))
+    return out
+
+
+def te_matrix_info_get(H) -> dict:
+    info = te_matrix_info()
+    _check(None, lib().te_matrix_info_get(H, C.byref(info)))
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def te_matrix_export(ctx, H):
+    """(rowptr int32, col int32, val complex128) host copies of the CSR arrays."""
+    info = te_matrix_info_get(H)
+    rp = np.empty(info["d"] + 1, dtype=np.int32)
+    col = np.empty(info["nnz"], dtype=np.int32)
+    val = np.empty(info["nnz"], dtype=np.complex128)
+    _check(ctx, lib().te_matrix_export(ctx, H, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data),
+                                       C.c_void_p(val.ctypes.data), 0))
+    return rp, col, val
+
+
+def te_matrix_free(H) -> None:
+    lib().te_matrix_free(H)
+
+
+def te_spmv(ctx, H, x, y=None):
+    """y = H x; returns (y, Re <x, H x>)."""
+    d = te_matrix_info_get(H)["d"]
+    xp, xdev, xk = _vec_ptr(x, d)
+    if y is None:
+        if xdev:
+            import torch
+            y = torch.empty_like(x)
+        else:
+            y = np.empty(d, dtype=np.complex128)
+    yp, ydev, yk = _vec_ptr(y, d, writable=True)
+    if xdev != ydev:
+        raise ValueError("x and y must both be host or both be device buffers")
+    dot = C.c_double()
+    _check(ctx, lib().te_spmv(ctx, H, xp, yp, C.byref(dot), TE_PTR_DEVICE if xdev else 0))
+    return y, dot.value
+
+
+def te_evolve(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None,
+              v_out=None, allow=(TE_OK,)):
+    """exp(-iHt) v_in; returns (v_out, stats dict, status)."""
+    d = te_matrix_info_get(H)["d"]
+    ip, idev, ik = _vec_ptr(v_in, d)
+    if v_out is None:
+        if idev:
+            import torch
+            v_out = torch.empty_like(v_in)
+        else:
+            v_out = np.empty(d, dtype=np.complex128)
+    op, odev, ok = _vec_ptr(v_out, d, writable=True)
+    if idev != odev:
+        raise ValueError("v_in and v_out must both be host or both be device buffers")
+    o = opt if opt is not None else te_default_options()
+    o = te_options.from_buffer_copy(o)
+    o.flags = (o.flags & ~TE_PTR_DEVICE) | (TE_PTR_DEVICE if idev else 0)
+    st = te_stats()
+    s = lib().te_evolve(ctx, H, ip, float(t), float(tol), int(m), C.byref(o), op, C.byref(st))
+    _check(ctx, s, allow)
+    return v_out, st.as_dict(), s
+
+
+def te_submit(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None):
+    d = te_matrix_info_get(H)["d"]
+    ip, idev, ik = _vec_ptr(v_in, d)
+    o = te_options.from_buffer_copy(opt if opt is not None else te_default_options())
+    o.flags = (o.flags & ~TE_PTR_DEVICE) | (TE_PTR_DEVICE if idev else 0)
+    out = C.c_void_p()
+    _check(ctx, lib().te_submit(ctx, H, ip, float(t), float(tol), int(m), C.byref(o), C.byref(out)))
+    return out
+
+
+def te_poll(req, v_out=None, d: int | None = None):
+    """(status, stats dict); fills v_out (host array or device tensor) when finished."""
+    st = te_stats()
+    p = C.c_void_p(0)
+    keep = None
+    if v_out is not None:
+        p, _, keep = _vec_ptr(v_out, v_out.shape[0] if d is None else d, writable=True)
+    s = lib().te_poll(req, p, C.byref(st))
+    return s, st.as_dict()
+
+
+def te_wait(req, timeout_ms: float = -1.0, v_out=None):
+    st = te_stats()
+    p = C.c_void_p(0)
+    keep = None
+    if v_out is not None:
+        p, _, keep = _vec_ptr(v_out, v_out.shape[0], writable=True)
+    s = lib().te_wait(req, float(timeout_ms), p, C.byref(st))
+    return s, st.as_dict()
+
+
+def te_cancel(req) -> int:
+    return lib().te_cancel(req)
+
+
+def te_request_free(req) -> None:
+    lib().te_request_free(req)
+
+
+def te_set_memory_budget(ctx, nbytes: int) -> None:
+    _check(ctx, lib().te_set_memory_budget(ctx, int(nbytes)))

@@ -1,0 +1,72 @@
+"""CPU-side checks of the C ABI library: it builds, loads, exports every entry
+point declared in include/te.h, and reports the missing GPU as an error status."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, cuda_available
+
+
+@pytest.fixture(scope="module")
+def libte():
+    from paper_2205_15346_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "te.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(te_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary_calls():
+    names = header_functions()
+    for required in ["te_create", "te_destroy", "te_build_csr", "te_build_model", "te_evolve",
+                     "te_submit", "te_poll", "te_cancel", "te_request_free", "te_spmv",
+                     "te_matrix_free", "te_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_header_function(libte):
+    missing = [n for n in header_functions() if not hasattr(libte, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_header_function():
+    from paper_2205_15346_gb300 import te
+    assert set(header_functions()) <= set(te.exported_symbols())
+
+
+def test_host_only_entry_points(libte):
+    from paper_2205_15346_gb300 import te
+    assert "sm_103a" in te.te_version()
+    assert te.te_status_string(te.TE_ERR_STEP_UNDERFLOW) == "TE_ERR_STEP_UNDERFLOW"
+    o = te.te_default_options()
+    assert (o.gauss_n, o.n_substeps, o.t_step0, o.shrink, o.quad_rel_tol, o.quad_max_levels) == \
+        (20, 10, 0.1, 0.97, 1e-3, 15)
+
+
+def test_bose_basis_index_matches_oracle_host(libte):
+    """te_model_basis_index is host code: check it against the oracle's enumeration."""
+    import workloads as W
+    from oracle import models
+    from paper_2205_15346_gb300 import te
+    for K, N in [(3, 2), (5, 4), (8, 5)]:
+        p = W.bose_params(K, N, seed=1)
+        b = models.BoseBasis(K, N)
+        for i in range(0, len(b), max(1, len(b) // 37)):
+            assert te.te_model_basis_index(p, b.states[i]) == i
+    p = W.bose_params(4, 3, seed=1)
+    with pytest.raises(te.TEError):
+        te.te_model_basis_index(p, (1, 1, 0, 0))     # wrong particle number
+
+
+@pytest.mark.skipif(cuda_available(), reason="checks the no-device path")
+def test_create_without_device_reports_error(libte):
+    from paper_2205_15346_gb300 import te
+    with pytest.raises(te.TEError):
+        te.te_create(0, stream=0)

@@ -1,0 +1,76 @@
+"""te_spmv (the fused SpMV kernel in plain-product mode) against the oracle's
+sparse product, element by element, for every lanes-per-row variant."""
+import numpy as np
+import pytest
+import scipy.sparse
+
+import workloads as W
+from oracle import models
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(te):
+    c = te.te_create(0)
+    yield c
+    te.te_destroy(c)
+
+
+def check_spmv(te, ctx, H, A, seed, torch_dev=False):
+    d = A.shape[0]
+    x = W.complex_gaussian(seed, d)
+    ref = A @ x
+    if torch_dev:
+        import torch
+        y, dot = te.te_spmv(ctx, H, torch.from_numpy(x).cuda())
+        y = y.cpu().numpy()
+    else:
+        y, dot = te.te_spmv(ctx, H, x)
+    scale = (abs(A) @ abs(x))
+    assert np.all(np.abs(y - ref) <= 1e-14 * scale + 1e-300)
+    assert abs(dot - np.vdot(x, ref).real) <= 1e-12 * np.vdot(abs(x), scale).real
+    return y
+
+
+@pytest.mark.parametrize("params", [
+    W.tfim_params(12, 1), W.xxzdm_params(14, 2), W.xxzdm_params(9, 3, pbc=False),
+    W.bose_params(8, 6, 4), W.bose_params(12, 5, 5),
+], ids=lambda p: p["model"])
+def test_spmv_models(te, ctx, params):
+    H = te.te_build_model(ctx, params)
+    try:
+        check_spmv(te, ctx, H, models.build(params).to_scipy(), 11)
+        check_spmv(te, ctx, H, models.build(params).to_scipy(), 12, torch_dev=True)
+    finally:
+        te.te_matrix_free(H)
+
+
+@pytest.mark.parametrize("avg", [0.5, 2.5, 9.0, 30.0, 60.0, 140.0])
+def test_spmv_ragged_and_empty_rows(te, ctx, avg):
+    """Random rows of very different lengths (including empty rows): every lanes variant."""
+    d = 3001
+    u = W.uniform(int(avg * 10) + 3, 3 * d)
+    lens = np.floor(2 * avg * u[:d] ** 2).astype(np.int64)
+    lens[::17] = 0
+    rows = np.repeat(np.arange(d), lens)
+    n = rows.size
+    v = W.uniform(99, 3 * n)
+    cols = (v[:n] * d).astype(np.int64)
+    vals = (v[n:2 * n] - 0.5) + 1j * (v[2 * n:] - 0.5)
+    csr = models.coo_to_csr(d, rows, cols, vals)
+    A = csr.to_scipy()
+    H = te.te_build_csr(ctx, d, rows, cols, vals)
+    try:
+        check_spmv(te, ctx, H, A, 13)
+    finally:
+        te.te_matrix_free(H)
+
+
+def test_spmv_single_row(te, ctx):
+    H = te.te_build_csr(ctx, 1, [0], [0], [2.5 - 1j])
+    try:
+        y, dot = te.te_spmv(ctx, H, np.array([1j]))
+        assert y[0] == (2.5 - 1j) * 1j and dot == 2.5
+    finally:
+        te.te_matrix_free(H)
