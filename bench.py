@@ -1,0 +1,317 @@
+"""Benchmark: exp(-iHt)v solves/s on the XXZ chain with Dzyaloshinskii-Moriya phases.
+
+Workload: L = 22 periodic XXZ-DM chain (d = 4,194,304, nnz = 50,331,648,
+complex128 CSR), Neel initial state, t = 50, Krylov dimension m = 40,
+err_max = 1e-8.  One step = one complete solve (every restart of Algorithm 1:
+Lanczos with the fused SpMV, eigen-decomposition, error-integral step search,
+recombination).  Inputs (H: 1.0 GB, the Krylov basis: 2.8 GB) are far larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs under torch.distributed.run: one independent solve stream per GPU
+(replicas; the method has no exchange step), time = max over ranks.
+"""
+from __future__ import annotations
+
+import os
+
+# the oracle's BLAS-1 calls stay on one thread (the paper's setting, Sec. 5)
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse
+import hashlib
+import json
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "exp(-iHt)v solves/s and p50/p99 latency at bound 1e-8; SpMV HBM GB/s vs peak"
+WORKLOAD = "xxzdm_L22"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k1_spmv_lanczos_xxzdm_L22.md")
+K1_SOURCE = os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", "te_lanczos.cu")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def k1_source_hash() -> str:
+    with open(K1_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per K1 launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    txt = open(PROFILE_SUMMARY).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not b or h.group(1) != k1_source_hash():
+        return None
+    return float(b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle (CPU) timing
+
+def oracle_sample(wl, max_restarts: int = 1):
+    """Time the oracle on a bounded sample: its first `max_restarts` restarts of
+    the workload's solve.  Returns (solves/s estimate, wall seconds, time covered)."""
+    from oracle import krylov, models
+    A = models.build(wl["params"]).to_scipy()
+    v0 = W.initial_vector(wl["v0"], wl["d"])
+    t0 = time.perf_counter()
+    res = krylov.evolve(A, v0, wl["t"], wl["tol"], wl["m"], max_restarts=max_restarts)
+    wall = time.perf_counter() - t0
+    covered = abs(res.t_reached)
+    return (covered / wl["t"]) / wall, wall, covered, res
+
+
+def cpu_baseline_entry(wl):
+    rate, wall, covered, res = oracle_sample(wl, 1)
+    return {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy, 1 thread) first restart of the {wl['name']} solve: "
+                       f"{res.matvecs} matvecs, t advanced {covered:.4g} of {wl['t']} in {wall:.1f} s; "
+                       f"solves/s = (fraction of t covered) / wall time")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = W.workload(WORKLOAD)
+    rates, walls = [], []
+    for i in range(args.warmup + args.steps):
+        rate, wall, covered, res = oracle_sample(wl, 1)
+        if i >= args.warmup:
+            rates.append(rate)
+            walls.append(wall)
+    value = float(np.mean(rates))
+    line = {
+        "metric": METRIC, "impl": "reference", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * float(np.mean(walls)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
+        "config": config_block(wl, args),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: the oracle's first restart of the workload solve "
+                                   "(1 thread); solves/s = fraction of t covered / wall time"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(wl, args):
+    return {"workload": f"{wl['name']}: XXZ-DM chain L=22 periodic, d=4194304, nnz=50331648, "
+                        f"Neel v0, t={wl['t']}, m={wl['m']}, tol={wl['tol']}",
+            "global_batch": args.gpus, "parallelism": f"replicas{args.gpus}",
+            "l2": "inputs larger than L2 (H 1.0 GB, Krylov basis 2.8 GB); no flush"}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2205_15346_gb300 import te
+
+    wl = W.workload(WORKLOAD)
+    p, d, t, tol, m = wl["params"], wl["d"], wl["t"], wl["tol"], wl["m"]
+    ctx = te.te_create(local)
+    H = te.te_build_model(ctx, p)
+    info = te.te_matrix_info_get(H)
+    v0 = W.initial_vector(wl["v0"], d)
+    vin = torch.from_numpy(v0).cuda()
+    vout = torch.empty_like(vin)
+    opt = te.make_options(profile=True)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        te.te_evolve(ctx, H, vin, t, tol, m, opt, v_out=vout)
+    barrier()
+    lat, stats = [], []
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e_a = torch.cuda.Event(enable_timing=True)
+            e_b = torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            _, st, _ = te.te_evolve(ctx, H, vin, t, tol, m, opt, v_out=vout)
+            e_b.record(stream)
+            e_b.synchronize()
+            lat.append(e_a.elapsed_time(e_b))
+            stats.append(st)
+        ev1.record(stream)
+        barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist is not None:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = args.steps * world / elapsed
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    hin = torch.from_numpy(v0).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    opt_e2e = te.make_options()
+    te.te_evolve(ctx, H, hin.numpy(), t, tol, m, opt_e2e, v_out=hout.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        te.te_evolve(ctx, H, hin.numpy(), t, tol, m, opt_e2e, v_out=hout.numpy())
+    barrier()
+    e2e_elapsed = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([e2e_elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_elapsed = float(tt.item())
+    e2e_value = args.steps * world / e2e_elapsed
+
+    # roofline of the dominant kernel (K1, fused SpMV + alpha partials), live CUDA-event times
+    nnz = info["nnz"]
+    k1_bytes = 20 * nnz + 4 * (d + 1) + 48 * d
+    spmv_ms = sum(s["spmv_ms"] for s in stats)
+    spmv_n = sum(s["spmv_launches"] for s in stats)
+    k1_avg_s = spmv_ms / spmv_n / 1000.0
+    peaks, kind = measured_peaks()
+    achieved = k1_bytes / k1_avg_s / 1e9
+    restarts = [s["restarts"] for s in stats]
+    launches = sum(1 + s["restarts"] * (2 * m + 2) for s in stats)
+
+    te.te_matrix_free(H)
+    te.te_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "complex128", "data": "synthetic (seeded XXZ-DM parameters, Neel state)",
+            "config": config_block(wl, argparse.Namespace(gpus=world)),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": recorded_traffic(),
+                         "kernel": "k_spmv_lanczos (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)",
+                         "bytes_per_launch": k1_bytes, "avg_launch_ms": 1000.0 * k1_avg_s,
+                         "peak_kind": f"{kind} (MEASURED_PEAKS.json hbm_gbs, copy kernel)"},
+            "spmv_gbs": achieved,
+            "solve": {"restarts": restarts[0], "matvecs": stats[0]["matvecs"],
+                      "err_bound": stats[0]["err_bound"], "roundoff_est": stats[0]["roundoff_est"]},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 16 * d,
+                    "d2h_bytes_per_step": 16 * d},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_entry(wl)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

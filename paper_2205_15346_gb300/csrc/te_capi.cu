@@ -85,11 +85,13 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         const double2* x = p->V + (size_t)j * d;
         const double2* xprev = j > 0 ? p->V + (size_t)(j - 1) * d : nullptr;
         double2* y = p->V + (size_t)(j + 1) * d;
-        if (p->profile) e = cudaEventRecord(p->ev[2 * j], s);
+        // external event nodes: plain records inside a capture only order work
+        if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j], s, cudaEventRecordExternal);
         if (e == cudaSuccess)
             e = launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
                                     p->grid_k1, s);
-        if (p->profile && e == cudaSuccess) e = cudaEventRecord(p->ev[2 * j + 1], s);
+        if (p->profile && e == cudaSuccess)
+            e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
         if (p->reorth) {
             e = launch_orth_norm(y, x, d, p->st, j, 1, 0, p->partials, p->grid_stream, s);
@@ -149,8 +151,7 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
                          std::string("allocating the solver workspace: ") + cudaGetErrorString(e));
     }
     memset(p->st_host, 0, sizeof(DevState));
-    if (cudaMemsetAsync(p->st, 0, sizeof(DevState), s) != cudaSuccess ||
-        step_prepare(m) != cudaSuccess) {
+    if (cudaMemsetAsync(p->st, 0, sizeof(DevState), s) != cudaSuccess) {
         free_plan(p);
         return set_error(ctx, TE_ERR_CUDA, "preparing the solver workspace");
     }
@@ -292,6 +293,8 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
                     if (cudaEventElapsedTime(&ms, p->ev[2 * j], p->ev[2 * j + 1]) == cudaSuccess) {
                         S.spmv_ms += ms;
                         S.spmv_launches += 1;
+                    } else {
+                        cudaGetLastError();
                     }
                 }
             }
@@ -328,6 +331,13 @@ te_status resolve_options(const te_options* opt, te_options* o) {
 }
 
 void worker_loop(te_ctx* ctx);
+
+// Make the context's device current and drop any error left in this thread's
+// CUDA runtime state by earlier, unrelated calls (kernel launch checks read it).
+void enter(te_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    cudaGetLastError();
+}
 
 // Order the context's stream after everything already queued on the caller's
 // stream (the caller's buffers may still be in production there).
@@ -428,6 +438,10 @@ te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
         return TE_ERR_OOM;
     }
     cudaMemset(c->spmv_st, 0, sizeof(DevState));
+    if (step_prepare() != cudaSuccess) {
+        te_destroy(c);
+        return TE_ERR_CUDA;
+    }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->budget = (int64_t)(0.8 * (double)free_b);
@@ -469,7 +483,7 @@ te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t*
     if (n_entries > 0 && (!rows || !cols || !vals))
         return set_error(ctx, TE_ERR_INVALID_ARG, "NULL input array");
     if ((flags & TE_INPUT_IS_CSR) && !rows) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL rowptr");
-    cudaSetDevice(ctx->device);
+    enter(ctx);
     if (te_status js = join_user_stream(ctx)) return js;
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     cudaStream_t s = ctx->stream;
@@ -577,7 +591,7 @@ te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t*
 te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out) {
     if (!ctx || !desc || !out) return TE_ERR_INVALID_ARG;
     *out = nullptr;
-    cudaSetDevice(ctx->device);
+    enter(ctx);
     te_matrix* H = new te_matrix();
     H->ctx = ctx;
     te_status st;
@@ -623,7 +637,7 @@ te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
 te_status te_matrix_export(te_ctx* ctx, const te_matrix* H, int32_t* rowptr, int32_t* col,
                            double* val, uint32_t flags) {
     if (!ctx || !H) return TE_ERR_INVALID_ARG;
-    cudaSetDevice(ctx->device);
+    enter(ctx);
     if (te_status js = join_user_stream(ctx)) return js;
     const cudaMemcpyKind k = (flags & TE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaStream_t s = ctx->stream;
@@ -661,7 +675,7 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
                   uint32_t flags) {
     if (!ctx || !H || !x || !y) return TE_ERR_INVALID_ARG;
     if (x == y) return set_error(ctx, TE_ERR_INVALID_ARG, "x and y must be distinct buffers");
-    cudaSetDevice(ctx->device);
+    enter(ctx);
     if (te_status js = join_user_stream(ctx)) return js;
     cudaStream_t s = ctx->stream;
     const bool dev = (flags & TE_PTR_DEVICE) != 0;
@@ -701,7 +715,7 @@ te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
     resolve_options(opt, &o);
     te_status s = check_solve_args(ctx, H, t, tol, m, o);
     if (s) return s;
-    cudaSetDevice(ctx->device);
+    enter(ctx);
     if ((s = join_user_stream(ctx))) return s;
     const int mu = (int)std::min<int64_t>(m, H->d);
     const int lanes = o.spmv_lanes ? o.spmv_lanes : H->lanes;
@@ -733,7 +747,7 @@ te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
     resolve_options(opt, &o);
     te_status s = check_solve_args(ctx, H, t, tol, m, o);
     if (s) return s;
-    cudaSetDevice(ctx->device);
+    enter(ctx);
     if ((s = join_user_stream(ctx))) return s;
     te_request* r = new te_request();
     r->ctx = ctx;
@@ -776,6 +790,7 @@ te_status te_poll(te_request* r, double* v_out, te_stats* st) {
             return cuda_error(r->ctx, cudaGetLastError(), "te_poll copy");
     }
     if (st) *st = r->stats;
+    if (r->result != TE_OK) set_error(r->ctx, r->result, r->err);
     return r->result;
 }
 
@@ -854,6 +869,8 @@ void worker_loop(te_ctx* ctx) {
         te_status res;
         te_stats S;
         memset(&S, 0, sizeof(S));
+        cudaGetLastError();
+        std::string msg;
         if (r->cancel.load()) {
             res = TE_ERR_CANCELLED;
         } else {
@@ -866,6 +883,10 @@ void worker_loop(te_ctx* ctx) {
                                 true, &S, &r->cancel);
                 release_plan(ctx, p);
             }
+            if (res != TE_OK) {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                msg = ctx->err;
+            }
             std::lock_guard<std::mutex> lk(ctx->qmu);
             ctx->in_use -= (int64_t)r->footprint;
         }
@@ -874,6 +895,7 @@ void worker_loop(te_ctx* ctx) {
             std::lock_guard<std::mutex> lk(r->mu);
             r->stats = S;
             r->result = res;
+            r->err = res == TE_ERR_CANCELLED ? std::string("request cancelled") : msg;
             r->state.store(2);
         }
         r->cv.notify_all();

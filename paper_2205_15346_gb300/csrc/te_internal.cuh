@@ -131,7 +131,7 @@ struct te_request {
     te_status result = TE_PENDING;
     std::mutex mu;
     std::condition_variable cv;
-    bool freed_by_user = false;
+    std::string err;                 // message of a failed request
 };
 
 struct te_ctx {
@@ -180,7 +180,7 @@ cudaError_t launch_recombine(double2* V, int64_t d, DevState* st, double* partia
 int spmv_grid(int lanes, int64_t d, int num_sms);
 int occupancy_grid_spmv(int lanes, int num_sms);
 int step_smem_bytes(int m);
-cudaError_t step_prepare(int m);
+cudaError_t step_prepare();
 
 // builders
 te_status build_tfim(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);

@@ -345,9 +345,11 @@ int step_smem_bytes(int m) {
                  sizeof(int) * m);
 }
 
-cudaError_t step_prepare(int m) {
+// The limit is a property of the function, shared by every plan and thread, so
+// it is set once to the size needed by the largest Krylov dimension.
+cudaError_t step_prepare() {
     return cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                step_smem_bytes(m));
+                                step_smem_bytes(TE_M_MAX));
 }
 
 cudaError_t launch_step(DevState* st, int m, cudaStream_t s) {

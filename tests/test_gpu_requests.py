@@ -40,7 +40,7 @@ def test_requests_match_solo_solves(te, ctx):
             H, v0, t, tol, m = mats[i % len(mats)]
             out = np.empty_like(v0)
             s, st = te.te_wait(r, 120000.0, out)
-            assert s == te.TE_OK
+            assert s == te.TE_OK, te.te_last_error(ctx)
             assert st["t_reached"] == t and st["err_bound"] <= tol
             assert np.linalg.norm(out - solo[i % len(mats)]) <= tol
             s2, _ = te.te_poll(r, None)
