@@ -129,11 +129,22 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle (CPU) timing
 
+_ORACLE_H = {}
+
+
+def oracle_matrix(wl):
+    from oracle import models
+    if wl["name"] not in _ORACLE_H:
+        _ORACLE_H[wl["name"]] = models.build(wl["params"]).to_scipy()
+    return _ORACLE_H[wl["name"]]
+
+
 def oracle_sample(wl, max_restarts: int = 1):
     """Time the oracle on a bounded sample: its first `max_restarts` restarts of
-    the workload's solve.  Returns (solves/s estimate, wall seconds, time covered)."""
-    from oracle import krylov, models
-    A = models.build(wl["params"]).to_scipy()
+    the workload's solve (matrix assembly excluded).  Returns (solves/s estimate,
+    wall seconds, time covered, result)."""
+    from oracle import krylov
+    A = oracle_matrix(wl)
     v0 = W.initial_vector(wl["v0"], wl["d"])
     t0 = time.perf_counter()
     res = krylov.evolve(A, v0, wl["t"], wl["tol"], wl["m"], max_restarts=max_restarts)
@@ -154,7 +165,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = W.workload(WORKLOAD)
+    wl = W.workload(args.workload)
     rates, walls = [], []
     for i in range(args.warmup + args.steps):
         rate, wall, covered, res = oracle_sample(wl, 1)
@@ -177,9 +188,16 @@ def run_reference(args):
     return 0
 
 
+DESCRIBE = {
+    "xxzdm_L22": "XXZ-DM chain L=22 periodic, d=4194304, nnz=50331648, Neel v0",
+    "xxzdm_L20": "XXZ-DM chain L=20 periodic, d=1048576, nnz=11534336, random v0",
+    "tfim_L12": "TFIM chain L=12 open, d=4096, nnz=53248, random v0",
+}
+
+
 def config_block(wl, args):
-    return {"workload": f"{wl['name']}: XXZ-DM chain L=22 periodic, d=4194304, nnz=50331648, "
-                        f"Neel v0, t={wl['t']}, m={wl['m']}, tol={wl['tol']}",
+    return {"workload": f"{wl['name']}: {DESCRIBE[wl['name']]}, "
+                        f"t={wl['t']}, m={wl['m']}, tol={wl['tol']}",
             "global_batch": args.gpus, "parallelism": f"replicas{args.gpus}",
             "l2": "inputs larger than L2 (H 1.0 GB, Krylov basis 2.8 GB); no flush"}
 
@@ -196,7 +214,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2205_15346_gb300 import te
 
-    wl = W.workload(WORKLOAD)
+    wl = W.workload(args.workload)
     p, d, t, tol, m = wl["params"], wl["d"], wl["t"], wl["tol"], wl["m"]
     ctx = te.te_create(local)
     H = te.te_build_model(ctx, p)
@@ -274,7 +292,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "complex128", "data": "synthetic (seeded XXZ-DM parameters, Neel state)",
-            "config": config_block(wl, argparse.Namespace(gpus=world)),
+            "config": config_block(wl, argparse.Namespace(gpus=world, workload=args.workload)),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
@@ -305,9 +323,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIBE))
     args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
+    args.warmup = max(args.warmup, 3)     # at least three untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
