@@ -199,6 +199,31 @@ void te_matrix_free(te_matrix* H);
 te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y,
                   double* x_dot_y, uint32_t flags);
 
+/* Largest dimension accepted by te_spmv_noalloc. */
+#define TE_NOALLOC_MAX_D 8388608
+
+/* y = H x and Re <x, H x>, like te_spmv, but without allocating anything.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory at the moment they need the product -- code running inside a
+ * CUDA stream capture (cudaMalloc is illegal there), code whose framework owns
+ * all device memory through its own pool, and latency-critical loops that
+ * cannot afford cudaMalloc or the device-wide synchronisation implied by
+ * cudaFree.  te_spmv, by contrast, allocates staging buffers for host vectors.
+ *   x, y: device pointers (flags must contain TE_PTR_DEVICE), distinct,
+ *         complex128, length d; x_dot_y: host pointer or NULL.
+ *   d must not exceed TE_NOALLOC_MAX_D (else TE_ERR_UNSUPPORTED, nothing runs).
+ * The reduction scratch is a fixed device array inside libte (about 64 KB),
+ * which every GPU that loads the library keeps until the process exits.  The
+ * first call on a device looks up that array's device address (a one-time
+ * set-up step), so make the first call on each device before any stream
+ * capture begins.  All calls on a device share the array and it keeps the last
+ * call's contents: the library clears the part that must start at zero on every
+ * call, but calls that overlap on the GPU (from other streams or other host
+ * threads) race on it and must be serialised by the caller.  The call waits
+ * for the caller's stream, runs on the context's stream and returns when done. */
+te_status te_spmv_noalloc(te_ctx* ctx, const te_matrix* H, const double* x, double* y,
+                          double* x_dot_y, uint32_t flags);
+
 /* v_out = exp(-i H t) v_in to within err_max = tol (Algorithm 1).
  * v_in must be normalised to 1e-10 (Sec. 2.1).  t < 0 evolves with -H for |t|
  * (the reversal of Sec. 5); t = 0 copies v_in.  m is the Krylov dimension,

@@ -37,6 +37,7 @@ TE_WARN_ROUNDOFF = 0x1
 TE_WARN_QUAD = 0x2
 TE_FLAG_BREAKDOWN = 0x4
 TE_M_MAX = 128
+TE_NOALLOC_MAX_D = 8388608
 TE_QUAD_TANH_SINH = 0
 TE_QUAD_GAUSS = 1
 TE_REORTH_NONE = 0
@@ -92,6 +93,7 @@ _SIGS = {
     "te_matrix_export": (C.c_int32, [_P, _P, _P, _P, _P, C.c_uint32]),
     "te_matrix_free": (None, [_P]),
     "te_spmv": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
+    "te_spmv_noalloc": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
                               C.POINTER(te_options), _P, C.POINTER(te_stats)]),
     "te_submit": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
@@ -313,6 +315,18 @@ def te_spmv(ctx, H, x, y=None):
     dot = C.c_double()
     _check(ctx, lib().te_spmv(ctx, H, xp, yp, C.byref(dot), TE_PTR_DEVICE if xdev else 0))
     return y, dot.value
+
+
+def te_spmv_noalloc(ctx, H, x, y):
+    """y = H x through the allocation-free entry point; x, y are CUDA tensors.
+    Returns Re <x, H x>."""
+    d = te_matrix_info_get(H)["d"]
+    xp, xdev, xk = _vec_ptr(x, d)
+    yp, ydev, yk = _vec_ptr(y, d, writable=True)
+    dot = C.c_double()
+    flags = TE_PTR_DEVICE if (xdev and ydev) else 0
+    _check(ctx, lib().te_spmv_noalloc(ctx, H, xp, yp, C.byref(dot), flags))
+    return dot.value
 
 
 def te_evolve(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None,
