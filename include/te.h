@@ -22,6 +22,9 @@
  *     they return.
  *   - Matrices are stored as CSR with int32 row pointers and column indices and
  *     complex128 values (20 bytes per stored entry); nnz must stay below 2^31.
+ *     The library also keeps a sliced-ELLPACK copy (32-row slices, rows sorted by
+ *     length within windows of 1024) for its default SpMV; the sort is a
+ *     symmetric permutation of the basis that te_evolve and te_spmv undo.
  */
 #ifndef TE_H_
 #define TE_H_
@@ -86,7 +89,8 @@ typedef struct te_options {
     int32_t  max_substeps;     /* cap on growth substeps per step (default 1000) */
     double   min_step_rel;     /* underflow when a step falls below this * |t| (default 1e-13) */
     uint32_t flags;            /* TE_PTR_DEVICE for v_in / v_out; TE_OPT_PROFILE */
-    int32_t  spmv_lanes;       /* lanes per CSR row in the SpMV (1..32, power of 2); 0 = automatic */
+    int32_t  spmv_lanes;       /* 0: sliced-ELLPACK SpMV, one lane per row (default);
+                                  1..32 (power of 2): CSR SpMV with that many lanes per row */
 } te_options;
 
 /* Per-solve report.  err_bound is the sum of the accepted step errors (the
@@ -106,6 +110,10 @@ typedef struct te_stats {
     double   spmv_ms;          /* TE_OPT_PROFILE: summed CUDA-event time of fused SpMV launches */
     int64_t  spmv_launches;    /* TE_OPT_PROFILE: launches summed in spmv_ms */
     double   solve_ms;         /* host wall time of the call */
+    int64_t  quad_integrals;   /* error integrals evaluated by the step search */
+    int64_t  quad_nodes;       /* integrand evaluations in those integrals */
+    double   eig_mcycles;      /* 1e6 SM cycles spent diagonalising H_m (all restarts) */
+    double   search_mcycles;   /* 1e6 SM cycles spent in the step search and omega */
 } te_stats;
 
 typedef struct te_matrix_info {
@@ -113,7 +121,8 @@ typedef struct te_matrix_info {
     int64_t nnz;               /* stored entries */
     double  norm1;             /* ||H||_1 = max absolute column sum (= max row sum for Hermitian H) */
     int32_t max_row_nnz;
-    int32_t spmv_lanes;        /* lanes per row chosen for this matrix */
+    int32_t spmv_lanes;        /* lanes per row the CSR kernel would use for this matrix */
+    int64_t sell_nnz;          /* entries of the sliced-ELLPACK copy, padding included */
 } te_matrix_info;
 
 /* Synthetic model Hamiltonians built on the device (Sec. 3: the matrix of an

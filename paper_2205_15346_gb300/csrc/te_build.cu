@@ -340,6 +340,31 @@ te_status alloc_matrix(te_ctx* ctx, te_matrix* H, int64_t d, int64_t nnz) {
     return TE_OK;
 }
 
+template <typename T>
+te_status upload(te_ctx* ctx, DevBuf<T>& buf, const T* host, size_t n, cudaStream_t s) {
+    TE_CUDA_TRY(ctx, buf.alloc(n));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.p, host, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return TE_OK;
+}
+
+void bose_tables(int K, int N, BoseTables* T) {
+    T->K = K;
+    T->N = N;
+    for (int n = 0; n < 16; ++n)
+        for (int k = 0; k < 17; ++k) {
+            // C(n + k - 1, k - 1) for k >= 1; no way to hold n > 0 bosons in 0 modes
+            if (k == 0) {
+                T->comp[n][k] = (n == 0) ? 1 : 0;
+                continue;
+            }
+            unsigned long long c = 1;
+            for (int i = 1; i <= k - 1; ++i) c = c * (unsigned long long)(n + i) / (unsigned long long)i;
+            T->comp[n][k] = c;
+        }
+}
+
+}  // namespace
+
 // rowptr from per-row counts; returns the total through *nnz.
 te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowptr, int64_t* nnz,
                       cudaStream_t s) {
@@ -370,31 +395,6 @@ te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowpt
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return TE_OK;
 }
-
-template <typename T>
-te_status upload(te_ctx* ctx, DevBuf<T>& buf, const T* host, size_t n, cudaStream_t s) {
-    TE_CUDA_TRY(ctx, buf.alloc(n));
-    TE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.p, host, n * sizeof(T), cudaMemcpyHostToDevice, s));
-    return TE_OK;
-}
-
-void bose_tables(int K, int N, BoseTables* T) {
-    T->K = K;
-    T->N = N;
-    for (int n = 0; n < 16; ++n)
-        for (int k = 0; k < 17; ++k) {
-            // C(n + k - 1, k - 1) for k >= 1; no way to hold n > 0 bosons in 0 modes
-            if (k == 0) {
-                T->comp[n][k] = (n == 0) ? 1 : 0;
-                continue;
-            }
-            unsigned long long c = 1;
-            for (int i = 1; i <= k - 1; ++i) c = c * (unsigned long long)(n + i) / (unsigned long long)i;
-            T->comp[n][k] = c;
-        }
-}
-
-}  // namespace
 
 te_status build_tfim(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
     const int L = m->L;

@@ -88,8 +88,9 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         // external event nodes: plain records inside a capture only order work
         if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j], s, cudaEventRecordExternal);
         if (e == cudaSuccess)
-            e = launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
-                                    p->grid_k1, s);
+            e = p->lanes ? launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
+                                               p->grid_k1, s)
+                         : launch_spmv_sell(H, x, xprev, y, p->st, j, 0, p->partials, p->grid_k1, s);
         if (p->profile && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
@@ -131,7 +132,7 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
     p->profile = profile;
     p->lanes = lanes;
     p->d = H->d;
-    p->grid_k1 = spmv_grid(lanes, H->d, ctx->num_sms);
+    p->grid_k1 = lanes ? spmv_grid(lanes, H->d, ctx->num_sms) : sell_grid(H->nslices, ctx->num_sms);
     const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
     p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
     p->grid_reorth = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 2);
@@ -262,7 +263,17 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->st, ini, sizeof(DevState), cudaMemcpyHostToDevice, s));
-    TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->V, v_in, sizeof(double2) * d, kin, s));
+    // the SELL kernel works in the length-sorted basis: v_in enters through perm
+    double2* stage = p->V + (size_t)p->m * d;          // column m is free outside a restart
+    const bool sell = (p->lanes == 0);
+    if (!sell) {
+        TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->V, v_in, sizeof(double2) * d, kin, s));
+    } else if (dev) {
+        TE_CUDA_TRY(ctx, launch_gather((const double2*)v_in, H->perm, d, p->V, ctx->num_sms, s));
+    } else {
+        TE_CUDA_TRY(ctx, cudaMemcpyAsync(stage, v_in, sizeof(double2) * d, kin, s));
+        TE_CUDA_TRY(ctx, launch_gather(stage, H->perm, d, p->V, ctx->num_sms, s));
+    }
     TE_CUDA_TRY(ctx, launch_init_norm(p->V, d, p->st, p->partials, p->grid_stream, s));
     TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -308,12 +319,23 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
             if (h->done) break;
         }
     }
-    TE_CUDA_TRY(ctx, cudaMemcpyAsync(v_out, p->V, sizeof(double2) * d, kout, s));
+    if (!sell) {
+        TE_CUDA_TRY(ctx, cudaMemcpyAsync(v_out, p->V, sizeof(double2) * d, kout, s));
+    } else if (dev) {
+        TE_CUDA_TRY(ctx, launch_gather(p->V, H->iperm, d, (double2*)v_out, ctx->num_sms, s));
+    } else {
+        TE_CUDA_TRY(ctx, launch_gather(p->V, H->iperm, d, stage, ctx->num_sms, s));
+        TE_CUDA_TRY(ctx, cudaMemcpyAsync(v_out, stage, sizeof(double2) * d, kout, s));
+    }
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     S.restarts = h->restarts;
     S.matvecs = h->matvecs;
     S.breakdowns = h->breakdowns;
     S.quad_warnings = h->quad_warnings;
+    S.quad_integrals = h->quad_integrals;
+    S.quad_nodes = h->quad_nodes;
+    S.eig_mcycles = 1e-6 * (double)h->eig_cycles;
+    S.search_mcycles = 1e-6 * (double)h->search_cycles;
     S.err_bound = h->err_acc;
     S.t_reached = (t >= 0.0 ? 1.0 : -1.0) * h->t_now;
     if (h->breakdowns) S.flags |= TE_FLAG_BREAKDOWN;
@@ -576,6 +598,7 @@ te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t*
         cudaMemcpyAsync(H->val, vv.data(), sizeof(double2) * nnz, cudaMemcpyHostToDevice, s);
     }
     te_status st = finish_matrix_stats(ctx, H);
+    if (st == TE_OK) st = build_sell(ctx, H);
     if (st) {
         te_matrix_free(H);
         return st;
@@ -602,6 +625,7 @@ te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out
         default: st = set_error(ctx, TE_ERR_INVALID_ARG, "unknown model");
     }
     if (st == TE_OK) st = finish_matrix_stats(ctx, H);
+    if (st == TE_OK) st = build_sell(ctx, H);
     if (st) {
         te_matrix_free(H);
         return st;
@@ -631,6 +655,7 @@ te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
     info->norm1 = H->norm1;
     info->max_row_nnz = H->max_row_nnz;
     info->spmv_lanes = H->lanes;
+    info->sell_nnz = H->sell_nnz;
     return TE_OK;
 }
 
@@ -663,9 +688,9 @@ void te_matrix_free(te_matrix* H) {
         }
         for (Plan* p : drop) free_plan(p);
     }
-    if (H->rowptr) cudaFree(H->rowptr);
-    if (H->col) cudaFree(H->col);
-    if (H->val) cudaFree(H->val);
+    for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
+                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val})
+        if (q) cudaFree(q);
     delete H;
 }
 
@@ -680,28 +705,34 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
     cudaStream_t s = ctx->stream;
     const bool dev = (flags & TE_PTR_DEVICE) != 0;
     const int64_t d = H->d;
-    double2 *xd = (double2*)x, *yd = (double2*)y;
-    double2 *xtmp = nullptr, *ytmp = nullptr;
-    if (!dev) {
-        TE_CUDA_TRY(ctx, cudaMalloc(&xtmp, sizeof(double2) * d));
-        if (cudaMalloc(&ytmp, sizeof(double2) * d) != cudaSuccess) {
-            cudaFree(xtmp);
-            return cuda_error(ctx, cudaErrorMemoryAllocation, "te_spmv scratch");
-        }
-        cudaMemcpyAsync(xtmp, x, sizeof(double2) * d, cudaMemcpyHostToDevice, s);
-        xd = xtmp;
-        yd = ytmp;
+    // the product runs in the length-sorted basis of the SELL form: x enters
+    // through perm, y leaves through iperm
+    double2 *xs = nullptr, *ys = nullptr;
+    TE_CUDA_TRY(ctx, cudaMalloc(&xs, sizeof(double2) * 2 * (size_t)d));
+    ys = xs + d;
+    cudaError_t e = cudaSuccess;
+    if (dev) {
+        e = launch_gather((const double2*)x, H->perm, d, xs, ctx->num_sms, s);
+    } else {
+        e = cudaMemcpyAsync(ys, x, sizeof(double2) * d, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_gather(ys, H->perm, d, xs, ctx->num_sms, s);
     }
-    const int grid = std::min(spmv_grid(H->lanes, d, ctx->num_sms), ctx->num_sms * 64);
-    cudaError_t e = launch_spmv_lanczos(H, H->lanes, xd, nullptr, yd, ctx->spmv_st, 0, 1,
-                                        ctx->spmv_partials, grid, s);
-    if (e == cudaSuccess && !dev)
-        e = cudaMemcpyAsync(y, yd, sizeof(double2) * d, cudaMemcpyDeviceToHost, s);
+    const int grid = std::min(sell_grid(H->nslices, ctx->num_sms), ctx->num_sms * 64);
+    if (e == cudaSuccess)
+        e = launch_spmv_sell(H, xs, nullptr, ys, ctx->spmv_st, 0, 1, ctx->spmv_partials, grid, s);
+    if (e == cudaSuccess) {
+        if (dev) {
+            e = launch_gather(ys, H->iperm, d, (double2*)y, ctx->num_sms, s);
+        } else {
+            e = launch_gather(ys, H->iperm, d, xs, ctx->num_sms, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(y, xs, sizeof(double2) * d, cudaMemcpyDeviceToHost, s);
+        }
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->spmv_st_host, ctx->spmv_st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (xtmp) cudaFree(xtmp);
-    if (ytmp) cudaFree(ytmp);
+    cudaFree(xs);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_spmv");
     if (x_dot_y) *x_dot_y = ctx->spmv_st_host->spmv_dot;
     return TE_OK;
@@ -718,7 +749,7 @@ te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
     enter(ctx);
     if ((s = join_user_stream(ctx))) return s;
     const int mu = (int)std::min<int64_t>(m, H->d);
-    const int lanes = o.spmv_lanes ? o.spmv_lanes : H->lanes;
+    const int lanes = o.spmv_lanes;          // 0: SELL (default), > 0: CSR with that many lanes
     Plan* p = nullptr;
     s = acquire_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, lanes, ctx->stream, &p);
     if (s) return s;
@@ -875,7 +906,7 @@ void worker_loop(te_ctx* ctx) {
             res = TE_ERR_CANCELLED;
         } else {
             Plan* p = nullptr;
-            const int lanes = r->opt.spmv_lanes ? r->opt.spmv_lanes : r->H->lanes;
+            const int lanes = r->opt.spmv_lanes;
             res = acquire_plan(ctx, r->H, r->m, r->opt.reorth,
                                (r->opt.flags & TE_OPT_PROFILE) ? 1 : 0, lanes, s, &p);
             if (res == TE_OK) {

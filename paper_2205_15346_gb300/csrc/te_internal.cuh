@@ -58,6 +58,10 @@ struct DevState {
     int64_t matvecs;
     int64_t breakdowns;
     int64_t quad_warnings;
+    int64_t quad_integrals;  // error integrals evaluated
+    int64_t quad_nodes;      // integrand evaluations
+    int64_t eig_cycles;      // SM cycles in the eigensolver (K3, summed over restarts)
+    int64_t search_cycles;   // SM cycles in the step search and omega (K3)
     // state of the current restart
     int32_t stop;            // inner Lanczos loop ended (breakdown)
     int32_t m_eff;
@@ -87,8 +91,16 @@ struct te_matrix {
     double2* val;            // device, nnz
     double norm1;
     int32_t max_row_nnz;
-    int32_t lanes;           // lanes per row for the SpMV
+    int32_t lanes;           // lanes per row for the CSR SpMV variant
     uint64_t id;
+    // sliced-ELLPACK copy in a length-sorted basis (te_sell.cu)
+    int32_t* perm = nullptr;     // new index -> old row (padded to a multiple of 32)
+    int32_t* iperm = nullptr;    // old row -> new index
+    int32_t* sell_off = nullptr; // slice offsets, nslices + 1
+    int32_t* sell_col = nullptr;
+    double2* sell_val = nullptr;
+    int64_t nslices = 0;
+    int64_t sell_nnz = 0;        // stored entries including padding
 };
 
 // One solve's device workspace and captured restart graph.
@@ -98,7 +110,7 @@ struct Plan {
     int m = 0;
     int reorth = 0;
     int profile = 0;
-    int lanes = 0;
+    int lanes = 0;                   // 0: SELL kernel in the permuted basis; > 0: CSR kernel
     int64_t d = 0;
     double2* V = nullptr;            // (m + 1) columns of length d, column-major
     DevState* st = nullptr;          // device
@@ -181,6 +193,17 @@ int spmv_grid(int lanes, int64_t d, int num_sms);
 int occupancy_grid_spmv(int lanes, int num_sms);
 int step_smem_bytes(int m);
 cudaError_t step_prepare();
+
+// SELL form (te_sell.cu)
+te_status build_sell(te_ctx* ctx, te_matrix* H);
+int sell_grid(int64_t nslices, int num_sms);
+cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
+                             double2* y, DevState* st, int j, int mode, double* partials, int grid,
+                             cudaStream_t s);
+cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
+                          int num_sms, cudaStream_t s);
+te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowptr, int64_t* nnz,
+                      cudaStream_t s);
 
 // builders
 te_status build_tfim(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);

@@ -1,0 +1,265 @@
+// te_sell.cu -- sliced-ELLPACK (SELL-C-sigma) form of H and the SpMV that uses it.
+//
+// On GB300 the FP64 pipe executes 2 lanes per SM per cycle (1.26 TFLOP/s for
+// the whole GPU), while a complex128 multiply-add costs 4 DFMA per stored entry
+// of 20 bytes.  The product y = H x is therefore bound by FP64 issue, not by
+// HBM, and the layout is chosen to waste no FP64 lane: one lane per row, 32
+// rows per slice (a warp), every row of a slice padded to the slice's widest
+// row, and rows sorted by length inside windows of kSigma rows so that padding
+// is rare.  No lane idles inside the loop and no shuffle reduction is needed.
+//
+// The sort is a symmetric permutation of the basis: new index i holds old row
+// perm[i], columns are renumbered through iperm, and the solver works on
+// permuted vectors (copied in and out once per solve).  Entries of slice s
+// are stored lane-interleaved: entry k of lane l sits at off[s] + 32 k + l, so
+// each warp load is 32 consecutive 16-byte values.  Padding entries hold 0 and
+// point at the lane's own row.
+#include <algorithm>
+
+#include "te_internal.cuh"
+
+namespace {
+
+constexpr int kSigma = 1024;     // rows per sorting window (multiple of 32)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    return warp_sum(r);
+}
+
+// ---------------------------------------------------------------- conversion
+
+// One block per window: rank of each row = rows that are longer, or equally
+// long with a smaller index (a stable descending sort by length).
+__global__ void __launch_bounds__(kSigma) k_sell_rank(const int32_t* __restrict__ rowptr, int64_t d,
+                                                      int32_t* __restrict__ perm,
+                                                      int32_t* __restrict__ iperm) {
+    __shared__ int32_t len[kSigma];
+    const int64_t base = (int64_t)blockIdx.x * kSigma;
+    const int n = (int)((d - base) < kSigma ? (d - base) : kSigma);
+    const int t = threadIdx.x;
+    if (t < n) len[t] = rowptr[base + t + 1] - rowptr[base + t];
+    __syncthreads();
+    if (t >= n) return;
+    const int mine = len[t];
+    int rank = 0;
+    for (int q = 0; q < n; ++q) {
+        const int l = len[q];
+        rank += (l > mine) || (l == mine && q < t);
+    }
+    perm[base + rank] = (int32_t)(base + t);
+    iperm[base + t] = (int32_t)(base + rank);
+}
+
+// Entries of slice s: 32 x (length of its first, longest row).
+__global__ void k_sell_width(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
+                             int64_t d, int64_t nslices, int32_t* __restrict__ cnt) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    const int64_t r = perm[s * 32];
+    cnt[s] = 32 * (rowptr[r + 1] - rowptr[r]);
+}
+
+__global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double2* __restrict__ val, const int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ iperm, const int32_t* __restrict__ off,
+                            int64_t d, int64_t nslices, int32_t* __restrict__ scol,
+                            double2* __restrict__ sval) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nslices * 32) return;
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int64_t o = off[s];
+    const int w = (off[s + 1] - off[s]) >> 5;
+    int b = 0, len = 0;
+    if (i < d) {
+        const int64_t old = perm[i];
+        b = rowptr[old];
+        len = rowptr[old + 1] - b;
+    }
+    const int32_t self = (int32_t)(i < d ? i : 0);
+    for (int k = 0; k < w; ++k) {
+        const int64_t p = o + 32ll * k + lane;
+        if (k < len) {
+            scol[p] = iperm[col[b + k]];
+            sval[p] = val[b + k];
+        } else {
+            scol[p] = self;
+            sval[p] = make_double2(0.0, 0.0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- SpMV
+
+__device__ __forceinline__ void cmac(double& re, double& im, const double2 a, const double2 x) {
+    re = fma(a.x, x.x, re);
+    re = fma(-a.y, x.y, re);
+    im = fma(a.x, x.y, im);
+    im = fma(a.y, x.x, im);
+}
+
+// mode 0: Lanczos step j (y = sign scale[j] H u_j - beta[j-1] scale[j-1] u_{j-1},
+// partial Re<u_j, y>, matvec count); mode 1: y = H x and Re<x, y>.
+__global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
+    const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+    const double2* __restrict__ val, const double2* __restrict__ x,
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    DevState* st, int j, int mode, double* partials) {
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    double cx = 1.0, bp = 0.0;
+    if (mode == 0) {
+        if (st->status != 0 || st->done != 0 || st->stop) return;
+        cx = st->sign * st->scale[j];
+        if (j > 0) bp = st->beta[j - 1] * st->scale[j - 1];
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc = 0.0;
+    for (int64_t s = warp; s < nslices; s += nwarps) {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const double2* vp = val + o + lane;
+        const int32_t* cp = col + o + lane;
+        double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+        int k = 0;
+        for (; k + 4 <= w; k += 4) {
+            const double2 a0 = __ldcs(vp + 32 * k), a1 = __ldcs(vp + 32 * (k + 1));
+            const double2 a2 = __ldcs(vp + 32 * (k + 2)), a3 = __ldcs(vp + 32 * (k + 3));
+            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+            const int c2 = __ldcs(cp + 32 * (k + 2)), c3 = __ldcs(cp + 32 * (k + 3));
+            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            const double2 x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+            cmac(re0, im0, a0, x0);
+            cmac(re1, im1, a1, x1);
+            cmac(re0, im0, a2, x2);
+            cmac(re1, im1, a3, x3);
+        }
+        for (; k < w; ++k) {
+            const double2 a0 = __ldcs(vp + 32 * k);
+            const double2 x0 = __ldg(x + __ldcs(cp + 32 * k));
+            cmac(re0, im0, a0, x0);
+        }
+        const int64_t row = s * 32 + lane;
+        if (row < d) {
+            const double re = re0 + re1, im = im0 + im1;
+            double2 out = make_double2(cx * re, cx * im);
+            if (bp != 0.0) {
+                const double2 p = __ldcs(xprev + row);
+                out.x = fma(-bp, p.x, out.x);
+                out.y = fma(-bp, p.y, out.y);
+            }
+            y[row] = out;
+            const double2 xr = __ldg(x + row);
+            acc = fma(xr.x, out.x, acc);
+            acc = fma(xr.y, out.y, acc);
+        }
+    }
+    const double sblk = block_sum(acc, sh);
+    unsigned int* ctr = &st->counter[1];
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = sblk;
+        __threadfence();
+        am_last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(partials + i);
+    const double tot = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        if (mode == 0) {
+            const double a = st->scale[j] * tot;
+            st->alpha[j] = a;
+            st->as_cur = a * st->scale[j];
+            st->matvecs += 1;
+        } else {
+            st->spmv_dot = tot;
+        }
+        *ctr = 0;
+    }
+}
+
+// dst[i] = src[map[i]]  (map = perm: old -> new order; map = iperm: back)
+__global__ void k_gather(const double2* __restrict__ src, const int32_t* __restrict__ map,
+                         int64_t d, double2* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[map[i]];
+}
+
+}  // namespace
+
+te_status build_sell(te_ctx* ctx, te_matrix* H) {
+    cudaStream_t s = ctx->stream;
+    const int64_t d = H->d;
+    const int64_t nslices = (d + 31) / 32;
+    const int64_t windows = (d + kSigma - 1) / kSigma;
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->perm, sizeof(int32_t) * (size_t)nslices * 32));
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->iperm, sizeof(int32_t) * (size_t)d));
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_off, sizeof(int32_t) * (size_t)(nslices + 1)));
+    // rows past d (in the last slice) map to row 0's length: give perm a valid entry there
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(H->perm, 0, sizeof(int32_t) * (size_t)nslices * 32, s));
+    k_sell_rank<<<(int)windows, kSigma, 0, s>>>(H->rowptr, d, H->perm, H->iperm);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int32_t* cnt = nullptr;
+    TE_CUDA_TRY(ctx, cudaMalloc(&cnt, sizeof(int32_t) * (size_t)nslices));
+    k_sell_width<<<(int)((nslices + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(H->rowptr, H->perm,
+                                                                                d, nslices, cnt);
+    cudaError_t e = cudaGetLastError();
+    int64_t total = 0;
+    te_status st = TE_OK;
+    if (e == cudaSuccess) st = scan_counts(ctx, cnt, nslices, H->sell_off, &total, s);
+    cudaFree(cnt);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "k_sell_width");
+    if (st) return st;
+    H->nslices = nslices;
+    H->sell_nnz = total;
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_col, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1)));
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_val, sizeof(double2) * (size_t)std::max<int64_t>(total, 1)));
+    k_sell_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
+        H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,
+        H->sell_val);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return TE_OK;
+}
+
+int sell_grid(int64_t nslices, int num_sms) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sell, TE_BLOCK, 0);
+    if (nb < 1) nb = 1;
+    const int64_t need = (nslices + (TE_BLOCK / 32) - 1) / (TE_BLOCK / 32);
+    const int64_t full = (int64_t)nb * num_sms;
+    return (int)std::max<int64_t>(1, std::min(need, full));
+}
+
+cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
+                             double2* y, DevState* st, int j, int mode, double* partials, int grid,
+                             cudaStream_t s) {
+    k_spmv_sell<<<grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_val, x, xprev, y, H->d,
+                                          H->nslices, st, j, mode, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
+                          int num_sms, cudaStream_t s) {
+    const int64_t want = (d + TE_BLOCK - 1) / TE_BLOCK;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * 8));
+    k_gather<<<grid, TE_BLOCK, 0, s>>>(src, map, d, dst);
+    return cudaGetLastError();
+}

@@ -85,13 +85,14 @@ struct Quad {
 // E(a, b); every thread gets the same value.  *warn counts non-converged calls
 // (incremented by thread 0 only).
 __device__ double integrate(const Integrand& F, const Quad& Qd, double a, double b, double* red,
-                            int* warn) {
+                            int* warn, long long* nodes) {
     if (a == b) return 0.0;
     const double c = 0.5 * (a + b), r = 0.5 * (b - a);
     const int tid = threadIdx.x, nt = blockDim.x;
     if (Qd.method == TE_QUAD_GAUSS) {
         double loc = 0.0;
         for (int i = tid; i < Qd.gauss_n; i += nt) loc += Qd.gw[i] * f_at(F, c + r * Qd.gx[i]);
+        if (tid == 0) *nodes += Qd.gauss_n;
         return r * block_sum_all(loc, red);
     }
     auto node = [&](double u, double& x, double& w) {
@@ -108,6 +109,7 @@ __device__ double integrate(const Integrand& F, const Quad& Qd, double a, double
         loc += w * f_at(F, x);
     }
     double total = block_sum_all(loc, red);
+    if (tid == 0) *nodes += 2 * j0 + 1;
     double step = 1.0;
     for (int level = 1; level <= Qd.max_levels; ++level) {
         step *= 0.5;
@@ -121,6 +123,7 @@ __device__ double integrate(const Integrand& F, const Quad& Qd, double a, double
             loc += w * f_at(F, x);
         }
         const double s = block_sum_all(loc, red);
+        if (tid == 0) *nodes += count;
         const double nt_total = 0.5 * total + step * s;
         if (level >= kMinLevel && fabs(nt_total - total) <= Qd.rel_tol * fabs(nt_total))
             return nt_total;
@@ -134,7 +137,9 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
     extern __shared__ double smem[];
     __shared__ double red[33];
     __shared__ int sh_mm, sh_nrot, sh_fail, sh_warn;
+    __shared__ long long sh_nodes;
     if (st->status != 0 || st->done != 0) return;
+    const long long clk0 = clock64();
     const int n = st->m_eff;
     const int tid = threadIdx.x, nt = blockDim.x;
     double2* ph = reinterpret_cast<double2*>(smem);   // 16-byte aligned first
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
     if (tid == 0) {
         sh_fail = 0;
         sh_warn = 0;
+        sh_nodes = 0;
     }
     __syncthreads();
 
@@ -244,6 +250,8 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
     }
     __syncthreads();
 
+    const long long clk1 = clock64();
+    int n_integrals = 0;
     // ---- 2-4. step size from the error integral
     const double h = st->beta[n - 1];
     const double T = st->T, t_now = st->t_now;
@@ -260,10 +268,10 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
     } else {
         if (st->first) {
             tau = fmin(st->t_step0, t_rem);
-            err = integrate(F, Qd, 0.0, tau, red, &sh_warn);
+            err = (++n_integrals, integrate(F, Qd, 0.0, tau, red, &sh_warn, &sh_nodes));
             if (err <= tol_rate * tau) {
                 while (2.0 * tau <= t_rem) {
-                    const double e2 = integrate(F, Qd, 0.0, 2.0 * tau, red, &sh_warn);
+                    const double e2 = (++n_integrals, integrate(F, Qd, 0.0, 2.0 * tau, red, &sh_warn, &sh_nodes));
                     if (!(e2 <= tol_rate * (2.0 * tau))) break;
                     tau = 2.0 * tau;
                     err = e2;
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
             }
         } else {
             tau = fmin(st->shrink * st->prev_step, t_rem);
-            err = integrate(F, Qd, 0.0, tau, red, &sh_warn);
+            err = (++n_integrals, integrate(F, Qd, 0.0, tau, red, &sh_warn, &sh_nodes));
         }
         while (!(err <= tol_rate * tau)) {
             tau = 0.5 * tau;
@@ -279,7 +287,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
                 underflow = true;
                 break;
             }
-            err = integrate(F, Qd, 0.0, tau, red, &sh_warn);
+            err = (++n_integrals, integrate(F, Qd, 0.0, tau, red, &sh_warn, &sh_nodes));
         }
         if (!underflow) {
             const double s = tau / st->n_substeps;
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
             int nsub = 0;
             while (nsub < st->max_substeps && tau < t_rem) {
                 const double end = fmin(base + (nsub + 1) * s, t_rem);
-                const double delta = integrate(F, Qd, tau, end, red, &sh_warn);
+                const double delta = (++n_integrals, integrate(F, Qd, tau, end, red, &sh_warn, &sh_nodes));
                 if (!(err + delta <= tol_rate * end)) break;
                 err += delta;
                 tau = end;
@@ -324,6 +332,10 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
         st->coef[r] = make_double2(sc * re, sc * im);
     }
     if (tid == 0) {
+        st->quad_integrals += n_integrals;
+        st->quad_nodes += sh_nodes;
+        st->eig_cycles += clk1 - clk0;
+        st->search_cycles += clock64() - clk1;
         st->t_now = (tau == t_rem) ? T : t_now + tau;
         st->err_acc += err;
         st->prev_step = tau;

@@ -61,7 +61,9 @@ class te_stats(C.Structure):
                 ("quad_warnings", C.c_int64), ("err_bound", C.c_double),
                 ("roundoff_est", C.c_double), ("t_reached", C.c_double), ("norm_in", C.c_double),
                 ("flags", C.c_uint32), ("m_used", C.c_int32), ("spmv_ms", C.c_double),
-                ("spmv_launches", C.c_int64), ("solve_ms", C.c_double)]
+                ("spmv_launches", C.c_int64), ("solve_ms", C.c_double),
+                ("quad_integrals", C.c_int64), ("quad_nodes", C.c_int64),
+                ("eig_mcycles", C.c_double), ("search_mcycles", C.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -69,7 +71,7 @@ class te_stats(C.Structure):
 
 class te_matrix_info(C.Structure):
     _fields_ = [("d", C.c_int64), ("nnz", C.c_int64), ("norm1", C.c_double),
-                ("max_row_nnz", C.c_int32), ("spmv_lanes", C.c_int32)]
+                ("max_row_nnz", C.c_int32), ("spmv_lanes", C.c_int32), ("sell_nnz", C.c_int64)]
 
 
 class te_model_desc(C.Structure):
