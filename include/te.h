@@ -68,6 +68,9 @@ typedef int32_t te_status;
 /* te_options.reorth */
 #define TE_REORTH_NONE 0           /* three-term recurrence of eq. arnoldi (default) */
 #define TE_REORTH_FULL 1           /* also classical Gram-Schmidt twice against all earlier vectors */
+/* te_options.small_exp: how exp(-i H_m tau) e_1 and the error integrand are evaluated */
+#define TE_SMALLEXP_CHEB 0         /* Chebyshev/Bessel (Jacobi-Anger) series of the tridiagonal H_m (default) */
+#define TE_SMALLEXP_EIG  1         /* diagonalisation of H_m, the paper's choice (Sec. 2.4) */
 /* te_options.flags */
 #define TE_OPT_PROFILE 0x10u       /* time every fused SpMV launch with CUDA events (te_stats.spmv_*) */
 
@@ -91,6 +94,8 @@ typedef struct te_options {
     uint32_t flags;            /* TE_PTR_DEVICE for v_in / v_out; TE_OPT_PROFILE */
     int32_t  spmv_lanes;       /* 0: sliced-ELLPACK SpMV, one lane per row (default);
                                   1..32 (power of 2): CSR SpMV with that many lanes per row */
+    int32_t  small_exp;        /* TE_SMALLEXP_CHEB (default) or TE_SMALLEXP_EIG */
+    int32_t  reserved;
 } te_options;
 
 /* Per-solve report.  err_bound is the sum of the accepted step errors (the

@@ -90,7 +90,7 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         if (e == cudaSuccess)
             e = p->lanes ? launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
                                                p->grid_k1, s)
-                         : launch_spmv_sell(H, x, xprev, y, p->st, j, 0, p->partials, p->grid_k1, s);
+                         : launch_spmv_sell(H, x, xprev, y, p->st, j, 0, p->partials, s);
         if (p->profile && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
@@ -132,7 +132,7 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
     p->profile = profile;
     p->lanes = lanes;
     p->d = H->d;
-    p->grid_k1 = lanes ? spmv_grid(lanes, H->d, ctx->num_sms) : sell_grid(H->nslices, ctx->num_sms);
+    p->grid_k1 = lanes ? spmv_grid(lanes, H->d, ctx->num_sms) : H->sell_grid;
     const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
     p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
     p->grid_reorth = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 2);
@@ -224,6 +224,8 @@ te_status check_solve_args(te_ctx* ctx, const te_matrix* H, double t, double tol
         return set_error(ctx, TE_ERR_INVALID_ARG, "gauss_n outside 2..64");
     if (o.n_substeps < 1 || o.max_substeps < 0)
         return set_error(ctx, TE_ERR_INVALID_ARG, "n_substeps >= 1 and max_substeps >= 0");
+    if (o.small_exp != TE_SMALLEXP_CHEB && o.small_exp != TE_SMALLEXP_EIG)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "unknown small_exp method");
     if (o.reorth != TE_REORTH_NONE && o.reorth != TE_REORTH_FULL)
         return set_error(ctx, TE_ERR_INVALID_ARG, "unknown reorth mode");
     if (!(o.t_step0 > 0.0) || !(o.shrink > 0.0 && o.shrink <= 1.0) || !(o.quad_rel_tol > 0.0) ||
@@ -257,6 +259,7 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     ini->gauss_n = o.gauss_n;
     ini->quad_max_levels = o.quad_max_levels;
     ini->max_substeps = o.max_substeps;
+    ini->smallexp = o.small_exp;
     ini->first = 1;
     ini->m_eff = p->m;
     gauss_legendre_nodes(o.gauss_n, ini->gx, ini->gw);
@@ -426,6 +429,7 @@ void te_default_options(te_options* o) {
     o->min_step_rel = 1e-13;
     o->flags = 0;
     o->spmv_lanes = 0;
+    o->small_exp = TE_SMALLEXP_CHEB;
 }
 
 const char* te_last_error(const te_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
@@ -689,7 +693,8 @@ void te_matrix_free(te_matrix* H) {
         for (Plan* p : drop) free_plan(p);
     }
     for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
-                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val})
+                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val,
+                    (void*)H->sell_warp})
         if (q) cudaFree(q);
     delete H;
 }
@@ -717,9 +722,8 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
         e = cudaMemcpyAsync(ys, x, sizeof(double2) * d, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = launch_gather(ys, H->perm, d, xs, ctx->num_sms, s);
     }
-    const int grid = std::min(sell_grid(H->nslices, ctx->num_sms), ctx->num_sms * 64);
     if (e == cudaSuccess)
-        e = launch_spmv_sell(H, xs, nullptr, ys, ctx->spmv_st, 0, 1, ctx->spmv_partials, grid, s);
+        e = launch_spmv_sell(H, xs, nullptr, ys, ctx->spmv_st, 0, 1, ctx->spmv_partials, s);
     if (e == cudaSuccess) {
         if (dev) {
             e = launch_gather(ys, H->iperm, d, (double2*)y, ctx->num_sms, s);

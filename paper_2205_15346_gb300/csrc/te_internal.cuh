@@ -46,6 +46,8 @@ struct DevState {
     int32_t gauss_n;
     int32_t quad_max_levels;
     int32_t max_substeps;
+    int32_t smallexp;        // TE_SMALLEXP_*
+    int32_t pad1;
     // progress of the solve
     double t_now;
     double prev_step;
@@ -101,6 +103,8 @@ struct te_matrix {
     double2* sell_val = nullptr;
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
+    int32_t* sell_warp = nullptr;  // first slice of each warp of the SpMV grid (+ end)
+    int sell_grid = 0;           // blocks of the SpMV grid the partition was built for
 };
 
 // One solve's device workspace and captured restart graph.
@@ -198,7 +202,7 @@ cudaError_t step_prepare();
 te_status build_sell(te_ctx* ctx, te_matrix* H);
 int sell_grid(int64_t nslices, int num_sms);
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
-                             double2* y, DevState* st, int j, int mode, double* partials, int grid,
+                             double2* y, DevState* st, int j, int mode, double* partials,
                              cudaStream_t s);
 cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
                           int num_sms, cudaStream_t s);

@@ -15,6 +15,7 @@
 // each warp load is 32 consecutive 16-byte values.  Padding entries hold 0 and
 // point at the lane's own row.
 #include <algorithm>
+#include <vector>
 
 #include "te_internal.cuh"
 
@@ -112,11 +113,13 @@ __device__ __forceinline__ void cmac(double& re, double& im, const double2 a, co
 
 // mode 0: Lanczos step j (y = sign scale[j] H u_j - beta[j-1] scale[j-1] u_{j-1},
 // partial Re<u_j, y>, matvec count); mode 1: y = H x and Re<x, y>.
+// Warp w of the grid owns the contiguous slices [wsl[w], wsl[w+1]), chosen at
+// build time so that every warp has the same number of stored entries.
 __global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
     const int32_t* __restrict__ off, const int32_t* __restrict__ col,
     const double2* __restrict__ val, const double2* __restrict__ x,
-    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
-    DevState* st, int j, int mode, double* partials) {
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d,
+    const int32_t* __restrict__ wsl, DevState* st, int j, int mode, double* partials) {
     __shared__ double sh[32];
     __shared__ bool am_last;
     double cx = 1.0, bp = 0.0;
@@ -127,9 +130,9 @@ __global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t s_end = __ldg(wsl + warp + 1);
     double acc = 0.0;
-    for (int64_t s = warp; s < nslices; s += nwarps) {
+    for (int64_t s = __ldg(wsl + warp); s < s_end; ++s) {
         const int32_t o = __ldg(off + s);
         const int w = (__ldg(off + s + 1) - o) >> 5;
         const double2* vp = val + o + lane;
@@ -235,6 +238,22 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
         H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,
         H->sell_val);
     TE_CUDA_TRY(ctx, cudaGetLastError());
+    // balanced contiguous slice ranges, one per warp of the SpMV grid
+    H->sell_grid = sell_grid(nslices, ctx->num_sms);
+    const int64_t nwarps = (int64_t)H->sell_grid * (TE_BLOCK / 32);
+    std::vector<int32_t> offs(nslices + 1), wsl(nwarps + 1);
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(offs.data(), H->sell_off, sizeof(int32_t) * (nslices + 1),
+                                     cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int64_t sl = 0;
+    for (int64_t w = 0; w <= nwarps; ++w) {
+        const int64_t target = (total * w) / nwarps;
+        while (sl < nslices && offs[sl] < target) ++sl;
+        wsl[w] = (int32_t)(w == nwarps ? nslices : sl);
+    }
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_warp, sizeof(int32_t) * (nwarps + 1)));
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(H->sell_warp, wsl.data(), sizeof(int32_t) * (nwarps + 1),
+                                     cudaMemcpyHostToDevice, s));
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return TE_OK;
 }
@@ -248,11 +267,12 @@ int sell_grid(int64_t nslices, int num_sms) {
     return (int)std::max<int64_t>(1, std::min(need, full));
 }
 
+// The grid is the one the warp partition was built for (H->sell_grid).
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
-                             double2* y, DevState* st, int j, int mode, double* partials, int grid,
+                             double2* y, DevState* st, int j, int mode, double* partials,
                              cudaStream_t s) {
-    k_spmv_sell<<<grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_val, x, xprev, y, H->d,
-                                          H->nslices, st, j, mode, partials);
+    k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_val, x, xprev,
+                                                 y, H->d, H->sell_warp, st, j, mode, partials);
     return cudaGetLastError();
 }
 

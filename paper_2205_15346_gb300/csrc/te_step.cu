@@ -1,26 +1,36 @@
 // te_step.cu -- K3: step 2 of Algorithm 1 (arXiv 2205.15346) in one thread block.
 //
-// Per restart, with H_m the real symmetric tridiagonal Lanczos matrix
-// (alpha on the diagonal, beta off it) and h = h_{m+1,m}:
-//  1. diagonalise H_m = Q diag(lam) Q^T once (Sec. 2.4, first remark), by the
-//     implicit QL iteration with shifts (Golub and Van Loan, "Matrix
-//     Computations", Sec. 8.3): one thread runs the scalar sweep and records its
-//     Givens rotations, then every thread applies them to its own row of Q;
-//  2. error integrand f(tau) = h |e_m^T exp(-i H_m tau) e_1|
-//                            = h |sum_k Q[m,k] Q[1,k] e^{-i lam_k tau}|   (eq. errorIntegral);
-//  3. E(a, b) = int_a^b f by adaptive tanh-sinh (Takahasi and Mori 1974): step
-//     2^-k on |u| <= 3.15, relative stop |I_k - I_{k-1}| <= quad_rel_tol |I_k| from
-//     level 3, warning after quad_max_levels (Sec. 4); or the non-adaptive
-//     Gauss-Legendre option;
-//  4. step size: largest admissible step by the search of Algorithm 1 step 2
-//     (first restart: start at t_step0 and double; later: shrink the previous
-//     step; then halve while E(0, tau) > tol_rate tau; then grow by substeps of
-//     tau / n_substeps while the accumulated integral stays within tol_rate times
-//     the new end), every candidate clipped to the remaining time; after a lucky
-//     breakdown the whole remaining time is taken with the bound h * t_rem;
-//  5. omega = exp(-i H_m tau) e_1 = Q diag(e^{-i lam tau}) Q^T e_1
-//     (eq. krylovApproximation) and the recombination coefficients
-//     coef[k] = beta0 scale[k] omega_k for K4.
+// Per restart, with H_m = T the real symmetric tridiagonal Lanczos matrix
+// (alpha on the diagonal, beta off it) and h = h_{m+1,m}, K3
+//  a. evaluates the error integrand f(tau) = h |e_m^T exp(-i T tau) e_1| (eq. errorIntegral),
+//  b. integrates it, E(a, b) = int_a^b f, by adaptive tanh-sinh (Takahasi and Mori 1974):
+//     step 2^-k on |u| <= 3.15, stop when |I_k - I_{k-1}| <= quad_rel_tol |I_k| from
+//     level 3 on, warning after quad_max_levels (Sec. 4); or by the non-adaptive
+//     Gauss-Legendre option,
+//  c. searches the largest admissible step (Algorithm 1 step 2 and the Sec. 2.4
+//     remarks: first restart from t_step0 with doubling; later restarts from the
+//     shrunk previous step; halve while E(0, tau) > tol_rate tau; grow by
+//     substeps of tau / n_substeps while the accumulated integral stays within
+//     tol_rate times the new end; candidates clipped to the remaining time;
+//     after a lucky breakdown the whole remaining time with the bound h t_rem),
+//  d. forms omega = exp(-i T tau) e_1 (eq. krylovApproximation) and the
+//     recombination coefficients coef[k] = beta0 scale[k] omega_k for K4.
+//
+// exp(-i T tau) e_1 is evaluated in one of two ways:
+//  * diagonalisation (the paper's choice, Sec. 2.4): T = Q diag(lam) Q^T by the
+//    implicit QL iteration with shifts (Golub and Van Loan, "Matrix Computations",
+//    Sec. 8.3); one thread runs the scalar sweep, all threads apply its Givens
+//    rotations to their rows of Q; then f = h |sum_k Q[m,k] Q[1,k] e^{-i lam_k tau}|.
+//  * Chebyshev expansion (default): with [b - a, b + a] a Gershgorin interval
+//    of T and T~ = (T - b) / a, the Jacobi-Anger expansion gives
+//      exp(-i T tau) = e^{-i b tau} sum_k c_k (-i)^k J_k(a tau) T_k(T~),  c_0 = 1, c_k = 2,
+//    with Bessel functions J_k and Chebyshev polynomials T_k.  The integrand
+//    only needs the scalars g_k = e_m^T T_k(T~) e_1 (zero for k < m - 1), built
+//    by the three-term Chebyshev recurrence; each node then costs one backward
+//    Bessel recurrence (Miller's algorithm, normalised by J_0 + 2 sum J_2k = 1),
+//    with no sin/cos and no serial eigensolver.  GB300 issues FP64 at 2 lanes
+//    per SM per cycle, so the long serial FP64 chain of QL dominates a restart;
+//    the Chebyshev route is lane-parallel over quadrature nodes.
 // All threads run the same control flow: every decision is taken from values
 // reduced over the block and broadcast through shared memory.
 #include <float.h>
@@ -32,6 +42,9 @@ namespace {
 constexpr double kUMax = 3.15;
 constexpr int kMinLevel = 3;
 constexpr double kHalfPi = 1.5707963267948966;
+constexpr int kKcap = 3072;          // largest Chebyshev / Bessel index
+constexpr int kMillerExtra = 20;     // backward recurrence starts this far above the last term
+constexpr double kBig = 1e250, kSmall = 1e-250;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -55,14 +68,55 @@ __device__ double block_sum_all(double v, double* red) {
     return red[32];
 }
 
-struct Integrand {
-    const double* lam;
-    const double* q;
+// Block minimum and maximum broadcast to every thread.
+__device__ void block_minmax_all(double lo, double hi, double* red, double* out_lo, double* out_hi) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[wid] = lo;
+        red[16 + wid] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double l = red[0], h = red[16];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            l = fmin(l, red[w]);
+            h = fmax(h, red[16 + w]);
+        }
+        red[32] = l;
+        red[31] = h;
+    }
+    __syncthreads();
+    *out_lo = red[32];
+    *out_hi = red[31];
+    __syncthreads();
+}
+
+// Number of Bessel terms kept at argument z: J_k(z) is below 1e-30 past it.
+__device__ __forceinline__ int bessel_terms(double z) {
+    return (int)ceil(z + 10.0 * cbrt(z) + 30.0);
+}
+
+struct Small {                       // what the integrand needs, in shared memory
+    int method;                      // TE_SMALLEXP_*
     int n;
     double h;
+    // diagonalisation
+    const double* lam;
+    const double* q;                 // Q[m,k] Q[1,k]
+    // Chebyshev
+    double a, b, inv_a;
+    const double* g;                 // g_k = e_m^T T_k(T~) e_1, valid for k <= K
+    int K, M;                        // terms kept and start of the backward recurrence
 };
 
-__device__ __forceinline__ double f_at(const Integrand& F, double tau) {
+// f(tau) by the eigen-decomposition
+__device__ __forceinline__ double f_eig(const Small& F, double tau) {
     double re = 0.0, im = 0.0;
     for (int k = 0; k < F.n; ++k) {
         double s, c;
@@ -71,6 +125,49 @@ __device__ __forceinline__ double f_at(const Integrand& F, double tau) {
         im = fma(-F.q[k], s, im);
     }
     return F.h * sqrt(re * re + im * im);
+}
+
+// f(tau) by the Chebyshev expansion: |sum_k c_k (-i)^k J_k(a tau) g_k| with
+// J_k from Miller's backward recurrence J_{k-1} = (2k / z) J_k - J_{k+1},
+// started at F.M with J_{M+1} = 0 and normalised by J_0 + 2 sum J_{2k} = 1.
+// The loop length is the same in every lane (F.M), so warps never diverge.
+__device__ __forceinline__ double f_cheb(const Small& F, double tau) {
+    const double z = F.a * tau;
+    const int first = F.n - 1;       // g_k = 0 below this index
+    if (!(z > 1e-300)) return first == 0 ? F.h * fabs(F.g[0]) : 0.0;
+    const double inv = 2.0 / z;
+    double t = inv * F.M;            // 2k / z for the current k
+    double jp = 0.0, jc = 1e-300;    // J_{k+1}, J_k (unnormalised)
+    double S = 0.0, re = 0.0, im = 0.0;
+    for (int k = F.M; k >= 0; --k) {
+        if (k >= first && k <= F.K) {
+            const double c = (k == 0 ? 1.0 : 2.0) * F.g[k] * jc;
+            switch (k & 3) {
+                case 0: re += c; break;
+                case 1: im -= c; break;
+                case 2: re -= c; break;
+                default: im += c; break;
+            }
+        }
+        if ((k & 1) == 0) S += (k == 0) ? jc : 2.0 * jc;
+        if (k == 0) break;
+        const double jn = fma(t, jc, -jp);
+        jp = jc;
+        jc = jn;
+        t -= inv;
+        if (fabs(jc) > kBig) {
+            jc *= kSmall;
+            jp *= kSmall;
+            S *= kSmall;
+            re *= kSmall;
+            im *= kSmall;
+        }
+    }
+    return F.h * sqrt(re * re + im * im) / fabs(S);
+}
+
+__device__ __forceinline__ double f_at(const Small& F, double tau) {
+    return F.method == TE_SMALLEXP_EIG ? f_eig(F, tau) : f_cheb(F, tau);
 }
 
 struct Quad {
@@ -82,9 +179,39 @@ struct Quad {
     const double* gw;
 };
 
-// E(a, b); every thread gets the same value.  *warn counts non-converged calls
-// (incremented by thread 0 only).
-__device__ double integrate(const Integrand& F, const Quad& Qd, double a, double b, double* red,
+// Chebyshev vectors v_k = T_k(T~) e_1 (three buffers rotated in shared memory),
+// extended until g is valid up to index K.
+struct ChebState {
+    double* v[3];
+    int cur;                         // v[cur] = v_kdone, v[(cur + 2) % 3] = v_{kdone-1}
+    int kdone;
+};
+
+__device__ void cheb_extend(ChebState& cs, double* g, int K, int n, const double* alpha,
+                            const double* beta, double a_inv, double b) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    while (cs.kdone < K) {
+        const double* vc = cs.v[cs.cur];
+        const double* vp = cs.v[(cs.cur + 2) % 3];
+        double* vn = cs.v[(cs.cur + 1) % 3];
+        for (int i = tid; i < n; i += nt) {
+            double tv = (alpha[i] - b) * vc[i];
+            if (i > 0) tv = fma(beta[i - 1], vc[i - 1], tv);
+            if (i + 1 < n) tv = fma(beta[i], vc[i + 1], tv);
+            tv *= a_inv;
+            vn[i] = (cs.kdone == 0) ? tv : 2.0 * tv - vp[i];
+        }
+        __syncthreads();
+        if (tid == 0) g[cs.kdone + 1] = vn[n - 1];
+        cs.cur = (cs.cur + 1) % 3;
+        cs.kdone += 1;
+        __syncthreads();
+    }
+}
+
+// E(a, b); every thread gets the same value.  *warn counts non-converged calls and
+// *nodes the integrand evaluations (both updated by thread 0 only).
+__device__ double integrate(const Small& F, const Quad& Qd, double a, double b, double* red,
                             int* warn, long long* nodes) {
     if (a == b) return 0.0;
     const double c = 0.5 * (a + b), r = 0.5 * (b - a);
@@ -133,38 +260,65 @@ __device__ double integrate(const Integrand& F, const Quad& Qd, double a, double
     return total;
 }
 
-__global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap) {
-    extern __shared__ double smem[];
-    __shared__ double red[33];
-    __shared__ int sh_mm, sh_nrot, sh_fail, sh_warn;
-    __shared__ long long sh_nodes;
-    if (st->status != 0 || st->done != 0) return;
-    const long long clk0 = clock64();
-    const int n = st->m_eff;
+// Shared-memory carve-up (16-byte aligned blocks first).
+struct Layout {
+    double2* ph;     // mcap
+    double2* om;     // mcap
+    double* Zt;      // mcap * mcap (diagonalisation only)
+    double* dd;      // mcap: eigenvalues / working diagonal
+    double* ee;      // mcap
+    double* q;       // mcap
+    double* z0;      // mcap
+    double* rc;      // mcap
+    double* rs;      // mcap
+    double* al;      // mcap: alpha
+    double* be;      // mcap: beta
+    double* v3;      // 3 * mcap: Chebyshev vectors
+    double* g;       // kKcap: g_k
+    double* jk;      // kKcap: J_k for omega
+    int* ri;         // mcap
+};
+
+__device__ Layout carve(double* smem, int mcap, int method) {
+    Layout L;
+    L.ph = reinterpret_cast<double2*>(smem);
+    L.om = L.ph + mcap;
+    double* p = reinterpret_cast<double*>(L.om + mcap);
+    if (method == TE_SMALLEXP_EIG) {
+        L.Zt = p;
+        p += (size_t)mcap * mcap;
+    } else {
+        L.Zt = nullptr;
+    }
+    L.dd = p; p += mcap;
+    L.ee = p; p += mcap;
+    L.q = p; p += mcap;
+    L.z0 = p; p += mcap;
+    L.rc = p; p += mcap;
+    L.rs = p; p += mcap;
+    L.al = p; p += mcap;
+    L.be = p; p += mcap;
+    if (method == TE_SMALLEXP_EIG) {
+        L.v3 = L.g = L.jk = nullptr;
+    } else {
+        L.v3 = p; p += 3 * (size_t)mcap;
+        L.g = p; p += kKcap;
+        L.jk = p; p += kKcap;
+    }
+    L.ri = reinterpret_cast<int*>(p);
+    return L;
+}
+
+// Implicit QL with shifts on (dd, ee); eigenvectors accumulated into Zt
+// (Zt[k * n + r] = Q[r][k]).  Returns false if an eigenvalue needed more than 64
+// iterations.
+__device__ bool ql_eigen(const Layout& L, int n, int* sh_mm, int* sh_nrot, int* sh_fail) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    double2* ph = reinterpret_cast<double2*>(smem);   // 16-byte aligned first
-    double* Zt = reinterpret_cast<double*>(ph + mcap);  // Zt[k*n + r] = Q[r][k]
-    double* dd = Zt + (size_t)mcap * mcap;              // eigenvalues
-    double* ee = dd + mcap;
-    double* q = ee + mcap;
-    double* z0 = q + mcap;
-    double* rc = z0 + mcap;
-    double* rs = rc + mcap;
-    int* ri = reinterpret_cast<int*>(rs + mcap);
-
+    double* Zt = L.Zt;
+    double* dd = L.dd;
+    double* ee = L.ee;
     for (int i = tid; i < n * n; i += nt) Zt[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
-    for (int i = tid; i < n; i += nt) {
-        dd[i] = st->alpha[i];
-        ee[i] = (i + 1 < n) ? st->beta[i] : 0.0;
-    }
-    if (tid == 0) {
-        sh_fail = 0;
-        sh_warn = 0;
-        sh_nodes = 0;
-    }
     __syncthreads();
-
-    // ---- 1. implicit QL with shifts
     for (int l = 0; l < n; ++l) {
         int iter = 0;
         for (;;) {
@@ -175,11 +329,11 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
                     if (fabs(ee[mm]) <= DBL_EPSILON * tst) break;
                     ++mm;
                 }
-                sh_mm = mm;
-                sh_nrot = 0;
+                *sh_mm = mm;
+                *sh_nrot = 0;
                 if (mm != l) {
                     if (++iter > 64) {
-                        sh_fail = 1;
+                        *sh_fail = 1;
                     } else {
                         double g = (dd[l + 1] - dd[l]) / (2.0 * ee[l]);
                         double r = hypot(g, 1.0);
@@ -205,9 +359,9 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
                             p = s * r;
                             dd[i + 1] = g + p;
                             g = c * r - bb;
-                            rc[nrot] = c;
-                            rs[nrot] = s;
-                            ri[nrot] = i;
+                            L.rc[nrot] = c;
+                            L.rs[nrot] = s;
+                            L.ri[nrot] = i;
                             ++nrot;
                         }
                         if (!early) {
@@ -215,19 +369,19 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
                             ee[l] = g;
                             ee[mm] = 0.0;
                         }
-                        sh_nrot = nrot;
+                        *sh_nrot = nrot;
                     }
                 }
             }
             __syncthreads();
-            const bool converged = (sh_mm == l) || (sh_fail != 0);
-            const int nrot = sh_nrot;
+            const bool converged = (*sh_mm == l) || (*sh_fail != 0);
+            const int nrot = *sh_nrot;
             __syncthreads();                  // thread 0 may overwrite sh_* only after this
             if (converged) break;
             for (int r = tid; r < n; r += nt) {
                 for (int qd = 0; qd < nrot; ++qd) {
-                    const int i = ri[qd];
-                    const double c = rc[qd], s = rs[qd];
+                    const int i = L.ri[qd];
+                    const double c = L.rc[qd], s = L.rs[qd];
                     const double zi = Zt[i * n + r], zi1 = Zt[(i + 1) * n + r];
                     Zt[(i + 1) * n + r] = s * zi + c * zi1;
                     Zt[i * n + r] = c * zi - s * zi1;
@@ -235,30 +389,110 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
             }
             __syncthreads();
         }
-        if (sh_fail) break;
+        if (*sh_fail) break;
     }
-    if (sh_fail) {
-        if (tid == 0) {
-            st->status = TE_ERR_INTERNAL;
-            st->done = 1;
-        }
-        return;
+    return *sh_fail == 0;
+}
+
+__global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st, int mcap) {
+    extern __shared__ double smem[];
+    __shared__ double red[33];
+    __shared__ int sh_mm, sh_nrot, sh_fail, sh_warn;
+    __shared__ long long sh_nodes;
+    __shared__ double sh_S;
+    if (st->status != 0 || st->done != 0) return;
+    const long long clk0 = clock64();
+    const int n = st->m_eff;
+    const int method = st->smallexp;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const Layout L = carve(smem, mcap, method);
+    for (int i = tid; i < n; i += nt) {
+        L.al[i] = st->alpha[i];
+        L.be[i] = (i + 1 < n) ? st->beta[i] : 0.0;
+        L.dd[i] = L.al[i];
+        L.ee[i] = L.be[i];
     }
-    for (int k = tid; k < n; k += nt) {
-        z0[k] = Zt[k * n + 0];
-        q[k] = Zt[k * n + (n - 1)] * Zt[k * n + 0];
+    if (tid == 0) {
+        sh_fail = 0;
+        sh_warn = 0;
+        sh_nodes = 0;
     }
     __syncthreads();
 
-    const long long clk1 = clock64();
-    int n_integrals = 0;
-    // ---- 2-4. step size from the error integral
     const double h = st->beta[n - 1];
+    Small F;
+    F.method = method;
+    F.n = n;
+    F.h = h;
+    F.lam = L.dd;
+    F.q = L.q;
+    F.g = L.g;
+    F.K = 0;
+    F.M = 0;
+    ChebState cs{};
+    if (method == TE_SMALLEXP_EIG) {
+        // ---- diagonalisation of H_m
+        if (!ql_eigen(L, n, &sh_mm, &sh_nrot, &sh_fail)) {
+            if (tid == 0) {
+                st->status = TE_ERR_INTERNAL;
+                st->done = 1;
+            }
+            return;
+        }
+        for (int k = tid; k < n; k += nt) {
+            L.z0[k] = L.Zt[k * n + 0];
+            L.q[k] = L.Zt[k * n + (n - 1)] * L.Zt[k * n + 0];
+        }
+        F.a = F.b = F.inv_a = 0.0;
+    } else {
+        // ---- Gershgorin interval [b - a, b + a] and the Chebyshev recurrence start
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = tid; i < n; i += nt) {
+            const double rad = (i > 0 ? fabs(L.be[i - 1]) : 0.0) + (i + 1 < n ? fabs(L.be[i]) : 0.0);
+            lo = fmin(lo, L.al[i] - rad);
+            hi = fmax(hi, L.al[i] + rad);
+        }
+        block_minmax_all(lo, hi, red, &lo, &hi);
+        F.b = 0.5 * (hi + lo);
+        F.a = 0.5 * (hi - lo);
+        if (!(F.a > 0.0)) F.a = 1.0;          // n = 1: any positive a gives the same series
+        F.inv_a = 1.0 / F.a;
+        cs.v[0] = L.v3;
+        cs.v[1] = L.v3 + mcap;
+        cs.v[2] = L.v3 + 2 * mcap;
+        cs.cur = 0;
+        cs.kdone = 0;
+        for (int i = tid; i < n; i += nt) {
+            cs.v[0][i] = (i == 0) ? 1.0 : 0.0;
+            cs.v[2][i] = 0.0;
+        }
+        if (tid == 0) L.g[0] = (n == 1) ? 1.0 : 0.0;
+        __syncthreads();
+    }
+    const long long clk1 = clock64();
+
+    // ---- step size from the error integral
     const double T = st->T, t_now = st->t_now;
     const double t_rem = T - t_now;
     const double tol_rate = st->tol_rate;
-    Integrand F{dd, q, n, h};
     Quad Qd{st->quad, st->quad_rel_tol, st->quad_max_levels, st->gauss_n, st->gx, st->gw};
+    int n_integrals = 0;
+    // E over [lo_t, hi_t]; for the Chebyshev route first make sure g covers the
+    // largest argument a * hi_t (an integral that would need more than kKcap terms
+    // is reported as infinite, i.e. the step is rejected: a conservative outcome).
+    auto E = [&](double lo_t, double hi_t) -> double {
+        ++n_integrals;
+        if (method != TE_SMALLEXP_EIG) {
+            const double zmax = F.a * hi_t;
+            if (!(zmax < (double)(kKcap - kMillerExtra - 200))) return INFINITY;
+            const int K = bessel_terms(zmax);
+            if (K + kMillerExtra >= kKcap) return INFINITY;
+            cheb_extend(cs, L.g, K, n, L.al, L.be, F.inv_a, F.b);
+            F.K = K;
+            F.M = K + kMillerExtra;
+        }
+        return integrate(F, Qd, lo_t, hi_t, red, &sh_warn, &sh_nodes);
+    };
     double tau = 0.0, err = 0.0;
     bool underflow = false;
     const bool brk = st->breakdown != 0;
@@ -268,10 +502,10 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
     } else {
         if (st->first) {
             tau = fmin(st->t_step0, t_rem);
-            err = (++n_integrals, integrate(F, Qd, 0.0, tau, red, &sh_warn, &sh_nodes));
+            err = E(0.0, tau);
             if (err <= tol_rate * tau) {
                 while (2.0 * tau <= t_rem) {
-                    const double e2 = (++n_integrals, integrate(F, Qd, 0.0, 2.0 * tau, red, &sh_warn, &sh_nodes));
+                    const double e2 = E(0.0, 2.0 * tau);
                     if (!(e2 <= tol_rate * (2.0 * tau))) break;
                     tau = 2.0 * tau;
                     err = e2;
@@ -279,7 +513,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
             }
         } else {
             tau = fmin(st->shrink * st->prev_step, t_rem);
-            err = (++n_integrals, integrate(F, Qd, 0.0, tau, red, &sh_warn, &sh_nodes));
+            err = E(0.0, tau);
         }
         while (!(err <= tol_rate * tau)) {
             tau = 0.5 * tau;
@@ -287,7 +521,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
                 underflow = true;
                 break;
             }
-            err = (++n_integrals, integrate(F, Qd, 0.0, tau, red, &sh_warn, &sh_nodes));
+            err = E(0.0, tau);
         }
         if (!underflow) {
             const double s = tau / st->n_substeps;
@@ -295,7 +529,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
             int nsub = 0;
             while (nsub < st->max_substeps && tau < t_rem) {
                 const double end = fmin(base + (nsub + 1) * s, t_rem);
-                const double delta = (++n_integrals, integrate(F, Qd, tau, end, red, &sh_warn, &sh_nodes));
+                const double delta = E(tau, end);
                 if (!(err + delta <= tol_rate * end)) break;
                 err += delta;
                 tau = end;
@@ -313,23 +547,104 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
         return;
     }
 
-    // ---- 5. omega = Q diag(e^{-i lam tau}) Q^T e_1, recombination coefficients
-    for (int k = tid; k < n; k += nt) {
-        double s, c;
-        sincos(dd[k] * tau, &s, &c);
-        ph[k] = make_double2(c * z0[k], -s * z0[k]);
+    // ---- omega = exp(-i H_m tau) e_1
+    const double beta0 = st->beta0;
+    if (method == TE_SMALLEXP_EIG) {
+        for (int k = tid; k < n; k += nt) {
+            double s, c;
+            sincos(L.dd[k] * tau, &s, &c);
+            L.ph[k] = make_double2(c * L.z0[k], -s * L.z0[k]);
+        }
+        __syncthreads();
+        for (int r = tid; r < n; r += nt) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double z = L.Zt[k * n + r];
+                re = fma(z, L.ph[k].x, re);
+                im = fma(z, L.ph[k].y, im);
+            }
+            L.om[r] = make_double2(re, im);
+        }
+    } else {
+        const double z = F.a * tau;
+        const int K = min(bessel_terms(fmin(z, (double)kKcap)), kKcap - kMillerExtra - 1);
+        const int M = K + kMillerExtra;
+        if (tid == 0) {
+            // J_0..J_K(z) by Miller's backward recurrence, normalised by J_0 + 2 sum J_2k
+            double* J = L.jk;
+            if (!(z > 1e-300)) {
+                J[0] = 1.0;
+                for (int k = 1; k <= K; ++k) J[k] = 0.0;
+                sh_S = 1.0;
+            } else {
+                const double inv = 2.0 / z;
+                double t = inv * M, jp = 0.0, jc = 1e-300, S = 0.0;
+                for (int k = M; k >= 0; --k) {
+                    if (k <= K) J[k] = jc;
+                    if ((k & 1) == 0) S += (k == 0) ? jc : 2.0 * jc;
+                    if (k == 0) break;
+                    const double jn = fma(t, jc, -jp);
+                    jp = jc;
+                    jc = jn;
+                    t -= inv;
+                    if (fabs(jc) > kBig) {
+                        jc *= kSmall;
+                        jp *= kSmall;
+                        S *= kSmall;
+                        for (int q = k; q <= K; ++q) J[q] *= kSmall;
+                    }
+                }
+                sh_S = S;
+            }
+        }
+        __syncthreads();
+        const double invS = 1.0 / sh_S;
+        // sum_k c_k (-i)^k J_k T_k(T~) e_1, recomputing the Chebyshev vectors
+        double* v0 = L.v3;
+        double* v1 = L.v3 + mcap;
+        double* v2 = L.v3 + 2 * mcap;
+        double accr = 0.0, acci = 0.0;
+        for (int i = tid; i < n; i += nt) {
+            v0[i] = (i == 0) ? 1.0 : 0.0;
+            v2[i] = 0.0;
+        }
+        __syncthreads();
+        double* vc = v0;
+        double* vp = v2;
+        double* vn = v1;
+        for (int k = 0; k <= K; ++k) {
+            const double c = (k == 0 ? 1.0 : 2.0) * L.jk[k] * invS;
+            if (tid < n) {
+                const double x = vc[tid];
+                switch (k & 3) {
+                    case 0: accr = fma(c, x, accr); break;
+                    case 1: acci = fma(-c, x, acci); break;
+                    case 2: accr = fma(-c, x, accr); break;
+                    default: acci = fma(c, x, acci); break;
+                }
+            }
+            if (k == K) break;
+            for (int i = tid; i < n; i += nt) {
+                double tv = (L.al[i] - F.b) * vc[i];
+                if (i > 0) tv = fma(L.be[i - 1], vc[i - 1], tv);
+                if (i + 1 < n) tv = fma(L.be[i], vc[i + 1], tv);
+                tv *= F.inv_a;
+                vn[i] = (k == 0) ? tv : 2.0 * tv - vp[i];
+            }
+            __syncthreads();
+            double* tmp = vp;
+            vp = vc;
+            vc = vn;
+            vn = tmp;
+        }
+        double sb, cb;
+        sincos(F.b * tau, &sb, &cb);                // e^{-i b tau}
+        if (tid < n) L.om[tid] = make_double2(cb * accr + sb * acci, cb * acci - sb * accr);
     }
     __syncthreads();
-    const double beta0 = st->beta0;
     for (int r = tid; r < n; r += nt) {
-        double re = 0.0, im = 0.0;
-        for (int k = 0; k < n; ++k) {
-            const double z = Zt[k * n + r];
-            re = fma(z, ph[k].x, re);
-            im = fma(z, ph[k].y, im);
-        }
         const double sc = beta0 * st->scale[r];
-        st->coef[r] = make_double2(sc * re, sc * im);
+        st->coef[r] = make_double2(sc * L.om[r].x, sc * L.om[r].y);
     }
     if (tid == 0) {
         st->quad_integrals += n_integrals;
@@ -353,8 +668,11 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_step(DevState* st, int mcap
 }  // namespace
 
 int step_smem_bytes(int m) {
-    return (int)(sizeof(double) * ((size_t)m * m + 6 * (size_t)m) + sizeof(double2) * m +
-                 sizeof(int) * m);
+    const size_t eig = sizeof(double2) * 2 * m + sizeof(double) * ((size_t)m * m + 8 * (size_t)m) +
+                       sizeof(int) * m;
+    const size_t cheb = sizeof(double2) * 2 * m + sizeof(double) * (11 * (size_t)m + 2 * kKcap) +
+                        sizeof(int) * m;
+    return (int)(eig > cheb ? eig : cheb);
 }
 
 // The limit is a property of the function, shared by every plan and thread, so

@@ -43,6 +43,8 @@ TE_QUAD_GAUSS = 1
 TE_REORTH_NONE = 0
 TE_REORTH_FULL = 1
 TE_OPT_PROFILE = 0x10
+TE_SMALLEXP_CHEB = 0
+TE_SMALLEXP_EIG = 1
 TE_MODEL_TFIM = 1
 TE_MODEL_XXZDM = 2
 TE_MODEL_BOSE = 3
@@ -53,7 +55,7 @@ class te_options(C.Structure):
                 ("reorth", C.c_int32), ("t_step0", C.c_double), ("shrink", C.c_double),
                 ("quad_rel_tol", C.c_double), ("quad_max_levels", C.c_int32),
                 ("max_substeps", C.c_int32), ("min_step_rel", C.c_double), ("flags", C.c_uint32),
-                ("spmv_lanes", C.c_int32)]
+                ("spmv_lanes", C.c_int32), ("small_exp", C.c_int32), ("reserved", C.c_int32)]
 
 
 class te_stats(C.Structure):
@@ -190,6 +192,8 @@ def make_options(**kw) -> te_options:
     for k, v in kw.items():
         if k == "quad" and isinstance(v, str):
             v = {"tanh-sinh": TE_QUAD_TANH_SINH, "gauss": TE_QUAD_GAUSS}[v]
+        if k == "small_exp" and isinstance(v, str):
+            v = {"cheb": TE_SMALLEXP_CHEB, "eig": TE_SMALLEXP_EIG}[v]
         if k == "reorth" and isinstance(v, bool):
             v = TE_REORTH_FULL if v else TE_REORTH_NONE
         if k == "profile":

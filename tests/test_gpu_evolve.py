@@ -101,6 +101,18 @@ def test_every_spmv_variant(te, ctx, lanes):
     parity(te, ctx, p, W.random_state(49, 1 << 11), 3.0, 1e-8, 25, spmv_lanes=lanes)
 
 
+@pytest.mark.parametrize("small_exp", ["cheb", "eig"])
+@pytest.mark.parametrize("params,v0seed,t,tol,m", [
+    (W.xxzdm_params(10, seed=63), 64, 8.0, 1e-8, 30),
+    (W.tfim_params(11, seed=65), 66, -12.0, 1e-10, 40),
+    (W.bose_params(7, 4, seed=67), 68, 4.0, 1e-6, 15),
+], ids=["xxzdm10", "tfim11", "bose7_4"])
+def test_small_exponential_methods(te, ctx, small_exp, params, v0seed, t, tol, m):
+    """Both evaluations of exp(-i H_m tau) e_1 (Chebyshev series, diagonalisation)."""
+    d = models.build(params).d
+    parity(te, ctx, params, W.random_state(v0seed, d), t, tol, m, small_exp=small_exp)
+
+
 @pytest.mark.parametrize("quad,reorth", [("gauss", False), ("tanh-sinh", True), ("gauss", True)])
 def test_options(te, ctx, quad, reorth):
     p = W.xxzdm_params(10, seed=50)
