@@ -124,7 +124,7 @@ __device__ __forceinline__ double f_eig(const Small& F, double tau) {
         re = fma(F.q[k], c, re);
         im = fma(-F.q[k], s, im);
     }
-    return F.h * sqrt(re * re + im * im);
+    return F.h * hypot(re, im);
 }
 
 // f(tau) by the Chebyshev expansion: |sum_k c_k (-i)^k J_k(a tau) g_k| with
@@ -163,7 +163,8 @@ __device__ __forceinline__ double f_cheb(const Small& F, double tau) {
             im *= kSmall;
         }
     }
-    return F.h * sqrt(re * re + im * im) / fabs(S);
+    // hypot: the unnormalised sums can be near 1e-215, where re * re underflows
+    return F.h * hypot(re, im) / fabs(S);
 }
 
 __device__ __forceinline__ double f_at(const Small& F, double tau) {
