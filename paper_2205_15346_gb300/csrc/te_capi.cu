@@ -136,7 +136,8 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
     const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
     p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
     p->grid_reorth = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 2);
-    const int max_grid = std::max(p->grid_k1, p->grid_stream);
+    const int max_grid = (int)std::max<int64_t>(std::max(p->grid_k1, p->grid_stream),
+                                                lanes ? 0 : sell_partials(H));
     p->bytes = plan_bytes(H->d, m, reorth, max_grid);
     cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
     if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState));
@@ -693,8 +694,7 @@ void te_matrix_free(te_matrix* H) {
         for (Plan* p : drop) free_plan(p);
     }
     for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
-                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val,
-                    (void*)H->sell_warp})
+                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val})
         if (q) cudaFree(q);
     delete H;
 }
@@ -713,8 +713,10 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
     // the product runs in the length-sorted basis of the SELL form: x enters
     // through perm, y leaves through iperm
     double2 *xs = nullptr, *ys = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&xs, sizeof(double2) * 2 * (size_t)d));
+    TE_CUDA_TRY(ctx, cudaMalloc(&xs, sizeof(double2) * 2 * (size_t)d +
+                                         sizeof(double) * (size_t)sell_partials(H)));
     ys = xs + d;
+    double* parts = reinterpret_cast<double*>(ys + d);
     cudaError_t e = cudaSuccess;
     if (dev) {
         e = launch_gather((const double2*)x, H->perm, d, xs, ctx->num_sms, s);
@@ -723,7 +725,7 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
         if (e == cudaSuccess) e = launch_gather(ys, H->perm, d, xs, ctx->num_sms, s);
     }
     if (e == cudaSuccess)
-        e = launch_spmv_sell(H, xs, nullptr, ys, ctx->spmv_st, 0, 1, ctx->spmv_partials, s);
+        e = launch_spmv_sell(H, xs, nullptr, ys, ctx->spmv_st, 0, 1, parts, s);
     if (e == cudaSuccess) {
         if (dev) {
             e = launch_gather(ys, H->iperm, d, (double2*)y, ctx->num_sms, s);

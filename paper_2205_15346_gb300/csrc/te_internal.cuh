@@ -103,8 +103,7 @@ struct te_matrix {
     double2* sell_val = nullptr;
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
-    int32_t* sell_warp = nullptr;  // first slice of each warp of the SpMV grid (+ end)
-    int sell_grid = 0;           // blocks of the SpMV grid the partition was built for
+    int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)
 };
 
 // One solve's device workspace and captured restart graph.
@@ -201,6 +200,7 @@ cudaError_t step_prepare();
 // SELL form (te_sell.cu)
 te_status build_sell(te_ctx* ctx, te_matrix* H);
 int sell_grid(int64_t nslices, int num_sms);
+int64_t sell_partials(const te_matrix* H);
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
                              double2* y, DevState* st, int j, int mode, double* partials,
                              cudaStream_t s);

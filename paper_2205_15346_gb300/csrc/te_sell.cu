@@ -22,6 +22,7 @@
 namespace {
 
 constexpr int kSigma = 1024;     // rows per sorting window (multiple of 32)
+constexpr int kChunk = 4;        // slices per work item of the SpMV
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -113,13 +114,17 @@ __device__ __forceinline__ void cmac(double& re, double& im, const double2 a, co
 
 // mode 0: Lanczos step j (y = sign scale[j] H u_j - beta[j-1] scale[j-1] u_{j-1},
 // partial Re<u_j, y>, matvec count); mode 1: y = H x and Re<x, y>.
-// Warp w of the grid owns the contiguous slices [wsl[w], wsl[w+1]), chosen at
-// build time so that every warp has the same number of stored entries.
-__global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
+//
+// Work is handed out in chunks of kChunk slices through an atomic counter, so
+// SMs that run slower (far-die L2 traffic, other streams) simply take fewer
+// chunks.  Each chunk stores its own partial of Re<x, y>; the last block adds
+// the chunk partials in chunk order, so the result does not depend on which
+// warp took which chunk.
+__global__ void __launch_bounds__(TE_BLOCK, 6) k_spmv_sell(
     const int32_t* __restrict__ off, const int32_t* __restrict__ col,
     const double2* __restrict__ val, const double2* __restrict__ x,
-    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d,
-    const int32_t* __restrict__ wsl, DevState* st, int j, int mode, double* partials) {
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    DevState* st, int j, int mode, double* partials) {
     __shared__ double sh[32];
     __shared__ bool am_last;
     double cx = 1.0, bp = 0.0;
@@ -129,52 +134,64 @@ __global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
         if (j > 0) bp = st->beta[j - 1] * st->scale[j - 1];
     }
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t s_end = __ldg(wsl + warp + 1);
-    double acc = 0.0;
-    for (int64_t s = __ldg(wsl + warp); s < s_end; ++s) {
-        const int32_t o = __ldg(off + s);
-        const int w = (__ldg(off + s + 1) - o) >> 5;
-        const double2* vp = val + o + lane;
-        const int32_t* cp = col + o + lane;
-        double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-        int k = 0;
-        for (; k + 4 <= w; k += 4) {
-            const double2 a0 = __ldcs(vp + 32 * k), a1 = __ldcs(vp + 32 * (k + 1));
-            const double2 a2 = __ldcs(vp + 32 * (k + 2)), a3 = __ldcs(vp + 32 * (k + 3));
-            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
-            const int c2 = __ldcs(cp + 32 * (k + 2)), c3 = __ldcs(cp + 32 * (k + 3));
-            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            const double2 x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-            cmac(re0, im0, a0, x0);
-            cmac(re1, im1, a1, x1);
-            cmac(re0, im0, a2, x2);
-            cmac(re1, im1, a3, x3);
-        }
-        for (; k < w; ++k) {
-            const double2 a0 = __ldcs(vp + 32 * k);
-            const double2 x0 = __ldg(x + __ldcs(cp + 32 * k));
-            cmac(re0, im0, a0, x0);
-        }
-        const int64_t row = s * 32 + lane;
-        if (row < d) {
-            const double re = re0 + re1, im = im0 + im1;
-            double2 out = make_double2(cx * re, cx * im);
-            if (bp != 0.0) {
-                const double2 p = __ldcs(xprev + row);
-                out.x = fma(-bp, p.x, out.x);
-                out.y = fma(-bp, p.y, out.y);
+    const int64_t nchunks = (nslices + kChunk - 1) / kChunk;
+    unsigned int* next = &st->counter[6];
+    for (;;) {
+        unsigned int c = 0;
+        if (lane == 0) c = atomicAdd(next, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((int64_t)c >= nchunks) break;
+        const int64_t s1 = ((int64_t)c + 1) * kChunk < nslices ? ((int64_t)c + 1) * kChunk : nslices;
+        double acc = 0.0;
+        for (int64_t s = (int64_t)c * kChunk; s < s1; ++s) {
+            const int32_t o = __ldg(off + s);
+            const int w = (__ldg(off + s + 1) - o) >> 5;
+            const double2* vp = val + o + lane;
+            const int32_t* cp = col + o + lane;
+            // one accumulator pair: the FP64 pipe, not the FMA latency, is the limit,
+            // and fewer registers keep six blocks resident per SM
+            double re = 0.0, im = 0.0;
+            int k = 0;
+            for (; k + 4 <= w; k += 4) {
+                const double2 a0 = __ldcs(vp + 32 * k), a1 = __ldcs(vp + 32 * (k + 1));
+                const double2 a2 = __ldcs(vp + 32 * (k + 2)), a3 = __ldcs(vp + 32 * (k + 3));
+                const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+                const int c2 = __ldcs(cp + 32 * (k + 2)), c3 = __ldcs(cp + 32 * (k + 3));
+                const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+                const double2 x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+                cmac(re, im, a0, x0);
+                cmac(re, im, a1, x1);
+                cmac(re, im, a2, x2);
+                cmac(re, im, a3, x3);
             }
-            y[row] = out;
-            const double2 xr = __ldg(x + row);
-            acc = fma(xr.x, out.x, acc);
-            acc = fma(xr.y, out.y, acc);
+            for (; k < w; ++k) {
+                const double2 a0 = __ldcs(vp + 32 * k);
+                const double2 x0 = __ldg(x + __ldcs(cp + 32 * k));
+                cmac(re, im, a0, x0);
+            }
+            const int64_t row = s * 32 + lane;
+            if (row < d) {
+                double2 out = make_double2(cx * re, cx * im);
+                if (bp != 0.0) {
+                    const double2 p = __ldcs(xprev + row);
+                    out.x = fma(-bp, p.x, out.x);
+                    out.y = fma(-bp, p.y, out.y);
+                }
+                y[row] = out;
+                const double2 xr = __ldg(x + row);
+                acc = fma(xr.x, out.x, acc);
+                acc = fma(xr.y, out.y, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            partials[c] = acc;
+            __threadfence();
         }
     }
-    const double sblk = block_sum(acc, sh);
+    __syncthreads();
     unsigned int* ctr = &st->counter[1];
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = sblk;
         __threadfence();
         am_last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
     }
@@ -182,7 +199,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
     if (!am_last) return;
     __threadfence();
     double v = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(partials + i);
+    for (int64_t i = threadIdx.x; i < nchunks; i += blockDim.x) v += __ldcg(partials + i);
     const double tot = block_sum(v, sh);
     if (threadIdx.x == 0) {
         if (mode == 0) {
@@ -194,6 +211,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_spmv_sell(
             st->spmv_dot = tot;
         }
         *ctr = 0;
+        *next = 0;
     }
 }
 
@@ -238,22 +256,7 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
         H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,
         H->sell_val);
     TE_CUDA_TRY(ctx, cudaGetLastError());
-    // balanced contiguous slice ranges, one per warp of the SpMV grid
     H->sell_grid = sell_grid(nslices, ctx->num_sms);
-    const int64_t nwarps = (int64_t)H->sell_grid * (TE_BLOCK / 32);
-    std::vector<int32_t> offs(nslices + 1), wsl(nwarps + 1);
-    TE_CUDA_TRY(ctx, cudaMemcpyAsync(offs.data(), H->sell_off, sizeof(int32_t) * (nslices + 1),
-                                     cudaMemcpyDeviceToHost, s));
-    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    int64_t sl = 0;
-    for (int64_t w = 0; w <= nwarps; ++w) {
-        const int64_t target = (total * w) / nwarps;
-        while (sl < nslices && offs[sl] < target) ++sl;
-        wsl[w] = (int32_t)(w == nwarps ? nslices : sl);
-    }
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_warp, sizeof(int32_t) * (nwarps + 1)));
-    TE_CUDA_TRY(ctx, cudaMemcpyAsync(H->sell_warp, wsl.data(), sizeof(int32_t) * (nwarps + 1),
-                                     cudaMemcpyHostToDevice, s));
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return TE_OK;
 }
@@ -267,12 +270,12 @@ int sell_grid(int64_t nslices, int num_sms) {
     return (int)std::max<int64_t>(1, std::min(need, full));
 }
 
-// The grid is the one the warp partition was built for (H->sell_grid).
+// partials must hold sell_partials(H) doubles (one per chunk of slices).
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
                              double2* y, DevState* st, int j, int mode, double* partials,
                              cudaStream_t s) {
     k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_val, x, xprev,
-                                                 y, H->d, H->sell_warp, st, j, mode, partials);
+                                                 y, H->d, H->nslices, st, j, mode, partials);
     return cudaGetLastError();
 }
 
@@ -283,3 +286,5 @@ cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, dou
     k_gather<<<grid, TE_BLOCK, 0, s>>>(src, map, d, dst);
     return cudaGetLastError();
 }
+
+int64_t sell_partials(const te_matrix* H) { return (H->nslices + kChunk - 1) / kChunk; }
