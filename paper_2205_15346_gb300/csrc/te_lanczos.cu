@@ -219,26 +219,31 @@ __global__ void __launch_bounds__(TE_BLOCK) k_orth_norm(double2* __restrict__ w,
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (; i + stride < d; i += 2 * stride) {
-        double2 y0 = w[i], y1 = w[i + stride];
-        const double2 u0 = __ldg(u + i), u1 = __ldg(u + i + stride);
-        y0.x -= as * u0.x;
-        y0.y -= as * u0.y;
-        y1.x -= as * u1.x;
-        y1.y -= as * u1.y;
-        if (write) {
-            w[i] = y0;
-            w[i + stride] = y1;
+    // four independent elements per trip keep enough loads in flight
+    for (; i + 3 * stride < d; i += 4 * stride) {
+        double2 yv[4], uv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            yv[q] = w[i + q * stride];
+            uv[q] = __ldg(u + i + q * stride);
         }
-        acc += y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            yv[q].x = fma(-as, uv[q].x, yv[q].x);
+            yv[q].y = fma(-as, uv[q].y, yv[q].y);
+            if (write) w[i + q * stride] = yv[q];
+            acc = fma(yv[q].x, yv[q].x, acc);
+            acc = fma(yv[q].y, yv[q].y, acc);
+        }
     }
-    if (i < d) {
+    for (; i < d; i += stride) {
         double2 y0 = w[i];
         const double2 u0 = __ldg(u + i);
-        y0.x -= as * u0.x;
-        y0.y -= as * u0.y;
+        y0.x = fma(-as, u0.x, y0.x);
+        y0.y = fma(-as, u0.y, y0.y);
         if (write) w[i] = y0;
-        acc += y0.x * y0.x + y0.y * y0.y;
+        acc = fma(y0.x, y0.x, acc);
+        acc = fma(y0.y, y0.y, acc);
     }
     if (!decide) return;
     const double s = block_sum(acc, sh);
