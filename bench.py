@@ -346,6 +346,91 @@ def run_ours(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a Poisson stream of mixed requests through te_submit / te_poll,
+    against the same requests solved one at a time (te_evolve)."""
+    import torch
+    from paper_2205_15346_gb300 import te
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = te.te_create(local)
+    pool = []
+    for fam, p in W.serve_pool():
+        H = te.te_build_model(ctx, p)
+        pool.append((H, te.te_matrix_info_get(H)["d"], p))
+    reqs = W.serve_requests(args.requests)
+    m = 40
+
+    def v0_for(k, seed):
+        H, d, p = pool[k]
+        return W.random_state(seed, d)
+
+    vins = [v0_for(k, sd) for (k, t, tol, sd, gap) in reqs]
+    # warm-up: one solve per pool entry (plans, graphs)
+    for H, d, p in pool:
+        te.te_evolve(ctx, H, W.random_state(1, d), 1.0, 1e-8, m)
+    # one at a time
+    solo_ms, solo_out = [], []
+    t0 = time.perf_counter()
+    for (k, t, tol, sd, gap), v in zip(reqs, vins):
+        a = time.perf_counter()
+        out, st, _ = te.te_evolve(ctx, pool[k][0], v, t, tol, m)
+        solo_ms.append(1000.0 * (time.perf_counter() - a))
+        solo_out.append(out)
+    solo_total = time.perf_counter() - t0
+    mean_solve = solo_total / len(reqs)
+    # served: submit at Poisson arrival times (all at t = 0 when --load 0), poll
+    if args.load > 0:
+        rate = args.load / mean_solve              # arrivals per second
+        arrivals = np.cumsum([gap / rate for (k, t, tol, sd, gap) in reqs])
+    else:
+        rate = float("inf")
+        arrivals = np.zeros(len(reqs))
+    pending, lat, done_out = {}, [0.0] * len(reqs), [None] * len(reqs)
+    nxt = 0
+    t0 = time.perf_counter()
+    while nxt < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            k, t, tol, sd, gap = reqs[nxt]
+            pending[nxt] = te.te_submit(ctx, pool[k][0], vins[nxt], t, tol, m)
+            nxt += 1
+        for i in list(pending):
+            s, st = te.te_poll(pending[i], None)
+            if s != te.TE_PENDING:
+                out = np.empty(pool[reqs[i][0]][1], dtype=np.complex128)
+                s, st = te.te_poll(pending[i], out)
+                if s != te.TE_OK:
+                    raise RuntimeError(f"request {i} failed: {te.te_status_string(s)}")
+                lat[i] = 1000.0 * (time.perf_counter() - t0 - arrivals[i])
+                done_out[i] = out
+                te.te_request_free(pending.pop(i))
+        time.sleep(0.0002)
+    served_total = time.perf_counter() - t0
+    worst = max(float(np.linalg.norm(a - b)) / r[2] for a, b, r in zip(done_out, solo_out, reqs))
+    line = {
+        "metric": METRIC, "mode": "serve", "value": len(reqs) / served_total, "unit": "solves/s",
+        "n_gpus": 1, "steps": len(reqs), "warmup": len(pool), "higher_is_better": True,
+        "ms_per_step": 1000.0 * served_total / len(reqs), "dtype": "complex128",
+        "data": "synthetic Poisson request mix (workloads.serve_requests, seed 5)",
+        "config": {"workload": (f"serving: {len(reqs)} requests over 12 Hamiltonians (TFIM/XXZ-DM "
+                                "2^10..2^22, bosons 1.2e4..1.1e6), t log-U[1,100], tol in "
+                                "{1e-6,1e-8,1e-10}, m=40"),
+                   "arrival_rate_per_s": rate if rate != float("inf") else None,
+                   "load_vs_one_at_a_time": args.load if args.load > 0 else "all at once"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "one_at_a_time": {"solves_per_s": len(reqs) / solo_total,
+                          "latency_ms_p50": float(np.percentile(solo_ms, 50)),
+                          "latency_ms_p99": float(np.percentile(solo_ms, 99))},
+        "max_diff_over_tol_vs_alone": worst,
+    }
+    for H, d, p in pool:
+        te.te_matrix_free(H)
+    te.te_destroy(ctx)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,11 +438,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIBE))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIBE) + ["serve_mix"])
+    ap.add_argument("--requests", type=int, default=32, help="serve_mix: number of requests")
+    ap.add_argument("--load", type=float, default=0.8,
+                    help="serve_mix: arrival rate as a fraction of one-at-a-time capacity "
+                         "(0: every request arrives at once)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)     # at least three untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve_mix":
+        return run_serve(args)
     return run_ours(args)
 
 

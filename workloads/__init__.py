@@ -166,3 +166,36 @@ def initial_vector(spec, d: int, index_of=None) -> np.ndarray:
             raise ValueError("occupation initial state needs an index_of callable")
         return basis_state(d, int(index_of(arg)))
     raise ValueError(kind)
+
+
+# ---------------------------------------------------------------- serving mix
+
+def serve_pool() -> list:
+    """Hamiltonians a serving stream draws from: spin chains of 2^10..2^22
+    states and number-conserving bosons of 1.2e4..1.1e6 states."""
+    pool = []
+    for i, L in enumerate((10, 14, 18, 22)):
+        pool.append(("tfim", tfim_params(L, seed=500 + i)))
+    for i, L in enumerate((12, 16, 20, 22)):
+        pool.append(("xxzdm", xxzdm_params(L, seed=510 + i)))
+    for i, (K, N) in enumerate(((12, 6), (14, 6), (14, 8), (14, 10))):
+        pool.append(("bose", bose_params(K, N, seed=520 + i)))
+    return pool
+
+
+def serve_requests(n: int, seed: int = 5) -> list:
+    """n requests: (pool index, t, tol, v0 seed, unit-rate exponential gap).
+
+    t ~ log-uniform on [1, 100], tol uniform over {1e-6, 1e-8, 1e-10}; the gap is
+    an Exp(1) draw that the caller divides by the arrival rate.
+    """
+    u = uniform(seed, 4 * n)
+    npool = len(serve_pool())
+    out = []
+    for i in range(n):
+        k = min(int(u[4 * i] * npool), npool - 1)
+        t = float(10.0 ** (2.0 * u[4 * i + 1]))
+        tol = (1e-6, 1e-8, 1e-10)[min(int(u[4 * i + 2] * 3), 2)]
+        gap = float(-np.log1p(-u[4 * i + 3]))
+        out.append((k, t, tol, 700 + i, gap))
+    return out
