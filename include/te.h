@@ -138,6 +138,13 @@ typedef struct te_matrix_info {
                              + sum_i c[i] Sz_i; e^{i phi_b} = a[b] + i b[b]; pbc -> L bonds, else L-1 */
 #define TE_MODEL_BOSE  3  /* H = sum_{i!=j} c_ij a_i^+ a_j + sum_i c[i] n_i^2 on K = L modes with N bosons;
                              c_ij = a[p] + i b[p] for i<j, p in (i-major, j-minor) order, c_ji = conj(c_ij) */
+#define TE_MODEL_MEMORY 4 /* the paper's example system (Sec. 5, eq. fullHamiltonianSimple):
+                             C0 (a0^+ b0 + h.c.) + em (1 - n0/Nc) sum_{k<=K} n_k
+                             + em (1 - n0/(Nc - dNc)) sum_{k'} n'_k'
+                             + Cm sum_{p<q} f(p,q) (a_p^+ a_q + h.c.) over all K + K' qubits;
+                             L = K, L2 = K', N = Nm excitations, N2 = N0 bosons in a_0, b_0;
+                             a = f(p,q) for p < q in (p-major, q-minor) order;
+                             p = {Nc, dNc, em, C0, Cm}.  Real symmetric. */
 typedef struct te_model_desc {
     int32_t model;             /* TE_MODEL_* */
     int32_t L;                 /* spins (chains, 3..30) or modes K (bosons, 2..16) */
@@ -147,6 +154,9 @@ typedef struct te_model_desc {
     const double* a;           /* see the model comments */
     const double* b;
     const double* c;
+    int32_t L2;                /* TE_MODEL_MEMORY: K' */
+    int32_t N2;                /* TE_MODEL_MEMORY: N0 */
+    const double* p;           /* TE_MODEL_MEMORY: {Nc, dNc, em, C0, Cm} */
 } te_model_desc;
 /* Basis conventions: spin chains use index bit i = 1 for spin i down
  * (sigma^z_i = -1).  Bosonic states are occupation tuples (n_0..n_{K-1}) with
@@ -190,8 +200,11 @@ te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t*
  * TE_ERR_UNSUPPORTED (size limits), TE_ERR_OOM. */
 te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out);
 
-/* Index of a bosonic occupation tuple occ[0..K-1] in the TE_MODEL_BOSE basis
- * (host-side ranking; TE_ERR_INVALID_ARG if the tuple is not in the basis). */
+/* Index of an occupation tuple in a model basis (host-side ranking;
+ * TE_ERR_INVALID_ARG if the tuple is not in the basis): TE_MODEL_BOSE takes
+ * occ[0..K-1]; TE_MODEL_MEMORY takes (n0, m0, q_1..q_{K+K'}), its basis ordered
+ * descending lexicographically (index = (N0 - n0) C(K+K', Nm) + rank of the
+ * qubit tuple). */
 te_status te_model_basis_index(const te_model_desc* desc, const int32_t* occ, int64_t* index);
 
 te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info);

@@ -225,6 +225,8 @@ def build(p: dict) -> CSR:
         return xxzdm_csr(p)
     if p["model"] == "bose":
         return bose_csr(p)
+    if p["model"] == "memory":
+        return memory_csr(p)
     raise ValueError(p["model"])
 
 
@@ -262,3 +264,122 @@ def spin_row(p: dict, r: int):
     entries.sort(key=lambda e: e[0])
     return (np.array([e[0] for e in entries], dtype=np.int64),
             np.array([e[1] for e in entries], dtype=np.complex128))
+
+
+# ---------------------------------------------------------------- the paper's example system
+
+class MemoryBasis:
+    """Basis of the paper's example system (Sec. 5): tuples (n0, m0, q_1..q_Q) with
+    n0 + m0 = N0 and exactly Nm of the Q = K + K' qubits excited, in descending
+    lexicographic order (n0 = N0 first).  Index = (N0 - n0) * C(Q, Nm) + position of
+    the qubit tuple among all qubit tuples in descending lexicographic order."""
+
+    def __init__(self, p: dict):
+        self.p = p
+        Q, Nm = p["K"] + p["Kp"], p["Nm"]
+        self.qconf = []
+        cur = [0] * Q
+
+        def rec(pos, rem):
+            if pos == Q:
+                if rem == 0:
+                    self.qconf.append(tuple(cur))
+                return
+            for bit in (1, 0):                         # 1 before 0: descending order
+                if bit > rem or Q - pos - 1 < rem - bit:
+                    continue
+                cur[pos] = bit
+                rec(pos + 1, rem - bit)
+            cur[pos] = 0
+
+        rec(0, Nm)
+        self.qindex = {q: i for i, q in enumerate(self.qconf)}
+        self.nq = len(self.qconf)
+
+    def __len__(self):
+        return (self.p["N0"] + 1) * self.nq
+
+    def state(self, r: int) -> tuple:
+        b, qi = divmod(r, self.nq)
+        n0 = self.p["N0"] - b
+        return (n0, self.p["N0"] - n0) + self.qconf[qi]
+
+    def index(self, s: tuple) -> int:
+        return (self.p["N0"] - s[0]) * self.nq + self.qindex[tuple(s[2:])]
+
+
+def _qpair(Q: int, p: int, q: int) -> int:
+    """Position of f(p, q), p < q (0-based qubits), in the (p-major, q-minor) table."""
+    return p * Q - p * (p + 1) // 2 + (q - p - 1)
+
+
+def memory_row(p: dict, basis: MemoryBasis, r: int):
+    """Row r of the example Hamiltonian (Sec. 5, eq. fullHamiltonianSimple):
+    C0 (a0^+ b0 + h.c.) + em (1 - n0/Nc) sum_k n_k + em (1 - n0/(Nc - dNc)) sum_k' n'_k'
+    + Cm sum_{p<q} f(p,q) (a_p^+ a_q + h.c.) over all qubit pairs.
+
+    Rounding order: diag = (em * (1 - n0 / Nc)) * n1 + (em * (1 - n0 / (Nc - dNc))) * n2;
+    boson hops C0 * (sqrt(.) * sqrt(.)); qubit hops Cm * f."""
+    K, Q = p["K"], p["K"] + p["Kp"]
+    n0, m0 = basis.state(r)[:2]
+    qs = basis.state(r)[2:]
+    n1, n2 = sum(qs[:K]), sum(qs[K:])
+    em, Nc, dNc = p["em"], p["Nc"], p["dNc"]
+    diag = (em * (1.0 - n0 / Nc)) * n1 + (em * (1.0 - n0 / (Nc - dNc))) * n2
+    entries = [(r, complex(diag, 0.0))]
+    if n0 >= 1:       # a0^+ b0 brings (n0 - 1, m0 + 1) to this state
+        amp = math.sqrt(float(n0)) * math.sqrt(float(m0 + 1))
+        entries.append((basis.index((n0 - 1, m0 + 1) + qs), complex(p["C0"] * amp, 0.0)))
+    if m0 >= 1:       # b0^+ a0 brings (n0 + 1, m0 - 1) to this state
+        amp = math.sqrt(float(m0)) * math.sqrt(float(n0 + 1))
+        entries.append((basis.index((n0 + 1, m0 - 1) + qs), complex(p["C0"] * amp, 0.0)))
+    for a in range(Q):
+        for b in range(a + 1, Q):
+            if qs[a] != qs[b]:
+                src = list(qs)
+                src[a], src[b] = qs[b], qs[a]
+                col = basis.index((n0, m0) + tuple(src))
+                entries.append((col, complex(p["Cm"] * p["f"][_qpair(Q, a, b)], 0.0)))
+    entries.sort(key=lambda e: e[0])
+    return (np.array([e[0] for e in entries], dtype=np.int64),
+            np.array([e[1] for e in entries], dtype=np.complex128))
+
+
+def memory_csr(p: dict, basis: MemoryBasis | None = None) -> CSR:
+    basis = basis or MemoryBasis(p)
+    d = len(basis)
+    cols, vals, lens = [], [], []
+    for r in range(d):
+        c, v = memory_row(p, basis, r)
+        cols.append(c)
+        vals.append(v)
+        lens.append(c.size)
+    rowptr = np.zeros(d + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(lens)
+    return CSR(d, rowptr, np.concatenate(cols), np.concatenate(vals))
+
+
+def memory_norm1(p: dict, basis: MemoryBasis | None = None) -> float:
+    """||H||_1 (maximum absolute row sum; H is real symmetric) of the example
+    Hamiltonian, vectorised over the basis without assembling H."""
+    basis = basis or MemoryBasis(p)
+    K, Q, N0 = p["K"], p["K"] + p["Kp"], p["N0"]
+    qc = np.array(basis.qconf, dtype=np.int64)                 # nq x Q
+    n1 = qc[:, :K].sum(axis=1).astype(np.float64)
+    n2 = qc[:, K:].sum(axis=1).astype(np.float64)
+    hop = np.zeros(len(qc))
+    for a in range(Q):
+        for b in range(a + 1, Q):
+            hop += (qc[:, a] != qc[:, b]) * abs(p["Cm"] * p["f"][_qpair(Q, a, b)])
+    best = 0.0
+    for n0 in range(N0 + 1):
+        m0 = N0 - n0
+        diag = np.abs((p["em"] * (1.0 - n0 / p["Nc"])) * n1
+                      + (p["em"] * (1.0 - n0 / (p["Nc"] - p["dNc"]))) * n2)
+        bos = 0.0
+        if n0 >= 1:
+            bos += abs(p["C0"] * math.sqrt(n0) * math.sqrt(m0 + 1))
+        if m0 >= 1:
+            bos += abs(p["C0"] * math.sqrt(m0) * math.sqrt(n0 + 1))
+        best = max(best, float(np.max(diag + hop + bos)))
+    return best

@@ -20,6 +20,7 @@
 namespace {
 
 constexpr int kBoseMaxEntries = 1 + 15 * 15;   // diagonal + n_occupied (K - 1), K <= 16, N <= 15
+constexpr int kMemMaxEntries = 3 + 15 * 15;    // diagonal, two boson hops, Nm (Q - Nm) qubit hops
 constexpr unsigned long long kEmpty = ~0ull;
 
 __device__ __forceinline__ double spin_sign(int64_t r, int i) {
@@ -247,6 +248,134 @@ __global__ void k_bose_fill(BoseTables T, const double* __restrict__ cre,
         col[p + i] = cs[i];
         val[p + i] = vs[i];
     }
+}
+
+
+// ---------------------------------------------------------------- the paper's example system
+
+struct MemTables {
+    int K, Q, Nm, N0;
+    long long nq;                        // C(Q, Nm)
+    long long C[32][32];                 // binomial coefficients C(n, k)
+    double Nc, dNc, em, C0, Cm;
+};
+
+// Qubit tuple of rank qi (descending lexicographic: 1 before 0 at each position).
+__device__ __host__ unsigned mem_unrank(const MemTables& T, long long qi) {
+    unsigned mask = 0;
+    int rem = T.Nm;
+    for (int pos = 0; pos < T.Q && rem > 0; ++pos) {
+        const long long with_one = T.C[T.Q - pos - 1][rem - 1];
+        if (qi < with_one) {
+            mask |= 1u << pos;
+            --rem;
+        } else {
+            qi -= with_one;
+        }
+    }
+    return mask;
+}
+
+__device__ __host__ long long mem_rank(const MemTables& T, unsigned mask) {
+    long long r = 0;
+    int rem = T.Nm;
+    for (int pos = 0; pos < T.Q && rem > 0; ++pos) {
+        if (mask & (1u << pos)) {
+            --rem;
+        } else {
+            r += T.C[T.Q - pos - 1][rem - 1];
+        }
+    }
+    return r;
+}
+
+__global__ void k_count_memory(MemTables T, int64_t d, int32_t* __restrict__ cnt) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    const long long b = r / T.nq;
+    const int n0 = T.N0 - (int)b, m0 = (int)b;
+    int c = 1 + (n0 >= 1) + (m0 >= 1) + T.Nm * (T.Q - T.Nm);
+    cnt[r] = c;
+}
+
+__global__ void k_fill_memory(MemTables T, const double* __restrict__ f, int64_t d,
+                              const int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                              double2* __restrict__ val, int* __restrict__ err) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    const long long b = r / T.nq, qi = r % T.nq;
+    const int n0 = T.N0 - (int)b, m0 = (int)b;
+    const unsigned mask = mem_unrank(T, qi);
+    const int n1 = __popc(mask & ((1u << T.K) - 1u));
+    const int n2 = __popc(mask) - n1;
+    int32_t cs[kMemMaxEntries];
+    double vs[kMemMaxEntries];
+    const double t1 = __dmul_rn(__dmul_rn(T.em, __dsub_rn(1.0, __ddiv_rn((double)n0, T.Nc))), (double)n1);
+    const double t2 = __dmul_rn(__dmul_rn(T.em, __dsub_rn(1.0, __ddiv_rn((double)n0, __dsub_rn(T.Nc, T.dNc)))),
+                                (double)n2);
+    int n = 0;
+    cs[n] = (int32_t)r;
+    vs[n] = __dadd_rn(t1, t2);
+    ++n;
+    if (n0 >= 1) {                           // a0^+ b0 brings (n0 - 1, m0 + 1) here
+        cs[n] = (int32_t)((b + 1) * T.nq + qi);
+        vs[n] = __dmul_rn(T.C0, __dmul_rn(sqrt((double)n0), sqrt((double)(m0 + 1))));
+        ++n;
+    }
+    if (m0 >= 1) {                           // b0^+ a0 brings (n0 + 1, m0 - 1) here
+        cs[n] = (int32_t)((b - 1) * T.nq + qi);
+        vs[n] = __dmul_rn(T.C0, __dmul_rn(sqrt((double)m0), sqrt((double)(n0 + 1))));
+        ++n;
+    }
+    for (int a = 0; a < T.Q; ++a) {
+        for (int c = a + 1; c < T.Q; ++c) {
+            const unsigned ba = (mask >> a) & 1u, bc = (mask >> c) & 1u;
+            if (ba == bc) continue;
+            const unsigned src = mask ^ (1u << a) ^ (1u << c);
+            cs[n] = (int32_t)(b * T.nq + mem_rank(T, src));
+            vs[n] = __dmul_rn(T.Cm, f[a * T.Q - a * (a + 1) / 2 + (c - a - 1)]);
+            ++n;
+        }
+    }
+    for (int i = 1; i < n; ++i) {
+        const int32_t kc = cs[i];
+        const double kv = vs[i];
+        int k = i - 1;
+        while (k >= 0 && cs[k] > kc) {
+            cs[k + 1] = cs[k];
+            vs[k + 1] = vs[k];
+            --k;
+        }
+        cs[k + 1] = kc;
+        vs[k + 1] = kv;
+    }
+    const int64_t p = rowptr[r];
+    if (rowptr[r + 1] - p != n) {
+        atomicExch(err, 1);
+        return;
+    }
+    for (int i = 0; i < n; ++i) {
+        col[p + i] = cs[i];
+        val[p + i] = make_double2(vs[i], 0.0);
+    }
+}
+
+void mem_tables(const te_model_desc* m, MemTables* T) {
+    memset(T, 0, sizeof(*T));
+    T->K = m->L;
+    T->Q = m->L + m->L2;
+    T->Nm = m->N;
+    T->N0 = m->N2;
+    for (int n = 0; n < 32; ++n) {
+        T->C[n][0] = 1;
+        for (int k = 1; k <= n; ++k) T->C[n][k] = T->C[n - 1][k - 1] + (k <= n - 1 ? T->C[n - 1][k] : 0);
+    }
+    T->nq = T->C[T->Q][T->Nm];
+    T->Nc = m->p[0];
+    T->dNc = m->p[1];
+    T->em = m->p[2];
+    T->C0 = m->p[3];
+    T->Cm = m->p[4];
 }
 
 // ---------------------------------------------------------------- scan and stats
@@ -551,4 +680,70 @@ int64_t bose_rank_host(int K, int N, const int32_t* occ) {
         rem -= occ[p];
     }
     return idx;
+}
+
+te_status build_memory(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
+    const int K = m->L, Kp = m->L2, Nm = m->N, N0 = m->N2;
+    if (K < 1 || Kp < 1 || K + Kp > 30 || Nm < 0 || Nm > K + Kp || N0 < 0 || !m->a || !m->p ||
+        (int64_t)Nm * (K + Kp - Nm) + 3 > kMemMaxEntries)
+        return set_error(ctx, TE_ERR_INVALID_ARG,
+                         "memory model needs K, K' >= 1, K + K' <= 30, 0 <= Nm <= K + K', N0 >= 0, "
+                         "Nm (K + K' - Nm) <= 225, the f table and 5 scalar parameters");
+    MemTables T;
+    mem_tables(m, &T);
+    const long long dd = (long long)(N0 + 1) * T.nq;
+    if (dd >= (1ll << 31)) return set_error(ctx, TE_ERR_UNSUPPORTED, "basis too large");
+    const int64_t d = dd;
+    cudaStream_t s = ctx->stream;
+    const int Q = K + Kp;
+    DevBuf<double> f;
+    DevBuf<int32_t> cnt;
+    DevBuf<int> err;
+    te_status st;
+    if ((st = upload(ctx, f, m->a, (size_t)std::max(Q * (Q - 1) / 2, 1), s))) return st;
+    TE_CUDA_TRY(ctx, cnt.alloc(d));
+    TE_CUDA_TRY(ctx, err.alloc(1));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    k_count_memory<<<grid_for(d), TE_BLOCK, 0, s>>>(T, d, cnt.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int32_t* rowptr = nullptr;
+    TE_CUDA_TRY(ctx, cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)));
+    int64_t nnz = 0;
+    if ((st = scan_counts(ctx, cnt.p, d, rowptr, &nnz, s))) {
+        cudaFree(rowptr);
+        return st;
+    }
+    H->d = d;
+    H->nnz = nnz;
+    H->rowptr = rowptr;
+    if (cudaMalloc(&H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
+        cudaMalloc(&H->val, sizeof(double2) * nnz) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
+    }
+    k_fill_memory<<<grid_for(d), TE_BLOCK, 0, s>>>(T, f.p, d, rowptr, H->col, H->val, err.p);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int herr = 0;
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (herr) return set_error(ctx, TE_ERR_INTERNAL, "memory model row length mismatch");
+    return TE_OK;
+}
+
+int64_t memory_rank_host(const te_model_desc* m, const int32_t* occ) {
+    MemTables T;
+    mem_tables(m, &T);
+    const int n0 = occ[0], m0 = occ[1];
+    if (n0 < 0 || m0 < 0 || n0 + m0 != T.N0) return -1;
+    unsigned mask = 0;
+    int ones = 0;
+    for (int q = 0; q < T.Q; ++q) {
+        if (occ[2 + q] != 0 && occ[2 + q] != 1) return -1;
+        if (occ[2 + q]) {
+            mask |= 1u << q;
+            ++ones;
+        }
+    }
+    if (ones != T.Nm) return -1;
+    return (long long)(T.N0 - n0) * T.nq + mem_rank(T, mask);
 }

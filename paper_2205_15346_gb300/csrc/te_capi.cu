@@ -627,6 +627,7 @@ te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out
         case TE_MODEL_TFIM: st = build_tfim(ctx, desc, H); break;
         case TE_MODEL_XXZDM: st = build_xxzdm(ctx, desc, H); break;
         case TE_MODEL_BOSE: st = build_bose(ctx, desc, H); break;
+        case TE_MODEL_MEMORY: st = build_memory(ctx, desc, H); break;
         default: st = set_error(ctx, TE_ERR_INVALID_ARG, "unknown model");
     }
     if (st == TE_OK) st = finish_matrix_stats(ctx, H);
@@ -645,6 +646,13 @@ te_status te_build_model(te_ctx* ctx, const te_model_desc* desc, te_matrix** out
 
 te_status te_model_basis_index(const te_model_desc* desc, const int32_t* occ, int64_t* index) {
     if (!desc || !occ || !index) return TE_ERR_INVALID_ARG;
+    if (desc->model == TE_MODEL_MEMORY) {
+        if (desc->L < 1 || desc->L2 < 1 || desc->L + desc->L2 > 30 || !desc->p) return TE_ERR_INVALID_ARG;
+        const int64_t r = memory_rank_host(desc, occ);
+        if (r < 0) return TE_ERR_INVALID_ARG;
+        *index = r;
+        return TE_OK;
+    }
     if (desc->model != TE_MODEL_BOSE || desc->L < 2 || desc->L > 16 || desc->N < 1 || desc->N > 15)
         return TE_ERR_INVALID_ARG;
     const int64_t r = bose_rank_host(desc->L, desc->N, occ);

@@ -213,6 +213,8 @@ te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowpt
 te_status build_tfim(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
 te_status build_xxzdm(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
 te_status build_bose(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
+te_status build_memory(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
+int64_t memory_rank_host(const te_model_desc* desc, const int32_t* occ);
 te_status finish_matrix_stats(te_ctx* ctx, te_matrix* H);
 int64_t bose_rank_host(int K, int N, const int32_t* occ);
 

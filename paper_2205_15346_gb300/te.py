@@ -48,6 +48,7 @@ TE_SMALLEXP_EIG = 1
 TE_MODEL_TFIM = 1
 TE_MODEL_XXZDM = 2
 TE_MODEL_BOSE = 3
+TE_MODEL_MEMORY = 4
 
 
 class te_options(C.Structure):
@@ -79,7 +80,8 @@ class te_matrix_info(C.Structure):
 class te_model_desc(C.Structure):
     _fields_ = [("model", C.c_int32), ("L", C.c_int32), ("N", C.c_int32), ("pbc", C.c_int32),
                 ("delta", C.c_double), ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
-                ("c", C.POINTER(C.c_double))]
+                ("c", C.POINTER(C.c_double)), ("L2", C.c_int32), ("N2", C.c_int32),
+                ("p", C.POINTER(C.c_double))]
 
 
 _P = C.c_void_p
@@ -252,6 +254,12 @@ def model_desc(params: dict):
         desc.b, k2 = _dptr(params["c_im"])
         desc.c, k3 = _dptr(params["U"])
         keep = [k1, k2, k3]
+    elif m == "memory":
+        desc.model, desc.L, desc.L2 = TE_MODEL_MEMORY, params["K"], params["Kp"]
+        desc.N, desc.N2 = params["Nm"], params["N0"]
+        desc.a, k1 = _dptr(params["f"] if len(params["f"]) else np.zeros(1))
+        desc.p, k2 = _dptr([params["Nc"], params["dNc"], params["em"], params["C0"], params["Cm"]])
+        keep = [k1, k2]
     else:
         raise ValueError(m)
     return desc, keep

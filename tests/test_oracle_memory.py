@@ -1,0 +1,110 @@
+"""Pins for the oracle's version of the paper's example system (Sec. 5): printed basis
+dimensions, a brute-force Fock-space construction, and the printed forward-backward
+bound at the paper's default parameters."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov, models
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_example_system.json")))
+
+
+@pytest.mark.parametrize("key", ["benchmark", "memory_limit_point"])
+def test_printed_dimensions(key):
+    g = GOLDEN[key]
+    p = W.memory_params(K=g["K"], Kp=g["Kp"], N0=g["N0"], Nm=g["Nm"], Nc=g["Nc"])
+    b = models.MemoryBasis(p)
+    assert b.nq == math.comb(g["K"] + g["Kp"], g["Nm"])
+    assert len(b) == g["printed_dimension"]
+    # order: all bosons in a_0 first, descending lexicographic qubit tuples
+    assert b.state(0) == (g["N0"], 0) + tuple([1] * g["Nm"] + [0] * (g["K"] + g["Kp"] - g["Nm"]))
+
+
+def test_coupling_table_reproduces_the_printed_rule():
+    """f_1, f_2, f_3 with the offsets Delta k_1 = Delta k_2 = 1, Delta k_3 = K+1,
+    Delta l_1 = Delta l_3 = K+1, Delta l_2 = 1 (Sec. 5), restated per sector."""
+    K = Kp = 4
+    p = W.memory_params(K=K, Kp=Kp)
+    Q = K + Kp
+
+    def f(Fv):
+        return Fv - 1.0 if Fv < 0.5 else Fv
+
+    def F(k, l, dk, dl):
+        return (math.sqrt(2.0) * (k + dk) ** 3 + math.sqrt(7.0) * (l + dl) ** 5) % 1.0
+    for k in range(1, K + 1):
+        for kp in range(1, Kp + 1):      # f_1(k, k'): qubits k and K + k'
+            assert abs(p["f"][models._qpair(Q, k - 1, K + kp - 1)] - f(F(k, kp, 1, K + 1))) < 1e-9
+        for l in range(k + 1, K + 1):    # f_2(k, l)
+            assert abs(p["f"][models._qpair(Q, k - 1, l - 1)] - f(F(k, l, 1, 1))) < 1e-9
+    for kp in range(1, Kp + 1):
+        for lp in range(kp + 1, Kp + 1):  # f_3(k', l')
+            assert abs(p["f"][models._qpair(Q, K + kp - 1, K + lp - 1)] - f(F(kp, lp, K + 1, K + 1))) < 1e-9
+
+
+def test_builder_against_fock_space():
+    """K = K' = 2, N0 = 3, Nm = 1: the full Fock space (a0, b0 up to 3 quanta, four
+    qubits) built from operator matrices, projected on the sector basis."""
+    p = W.memory_params(K=2, Kp=2, N0=3, Nm=1, Nc=3.0, dNc=1.0, em=0.7, C0=1.3, Cm=0.9)
+    b = models.MemoryBasis(p)
+    csr = models.memory_csr(p, b)
+    nb = 4
+    a = np.diag(np.sqrt(np.arange(1, nb)), k=1)
+    q = np.array([[0.0, 1.0], [0.0, 0.0]])
+    dims = [nb, nb, 2, 2, 2, 2]
+
+    def op(o, i):
+        mats = [np.eye(n) for n in dims]
+        mats[i] = o
+        out = mats[0]
+        for mm in mats[1:]:
+            out = np.kron(out, mm)
+        return out
+    A0, B0 = op(a, 0), op(a, 1)
+    Qs = [op(q, 2 + i) for i in range(4)]
+    n0 = A0.T @ A0
+    I = np.eye(A0.shape[0])
+    H = p["C0"] * (A0.T @ B0 + B0.T @ A0)
+    H += p["em"] * (I - n0 / p["Nc"]) @ (Qs[0].T @ Qs[0] + Qs[1].T @ Qs[1])
+    H += p["em"] * (I - n0 / (p["Nc"] - p["dNc"])) @ (Qs[2].T @ Qs[2] + Qs[3].T @ Qs[3])
+    for i in range(4):
+        for j in range(i + 1, 4):
+            c = p["Cm"] * p["f"][models._qpair(4, i, j)]
+            H += c * (Qs[i].T @ Qs[j] + Qs[j].T @ Qs[i])
+
+    def fock_index(s):
+        r = 0
+        for n, dim in zip(s, dims):
+            r = r * dim + n
+        return r
+    idx = [fock_index(b.state(r)) for r in range(len(b))]
+    np.testing.assert_allclose(csr.to_scipy().toarray(), H[np.ix_(idx, idx)], atol=1e-13, rtol=0)
+
+
+def test_forward_backward_at_default_parameters():
+    """The paper returns to the initial state with error 9.82e-9 within the
+    requested 2.0e-8 (t = 10, err_max = 1e-8)."""
+    g = GOLDEN["forward_backward"]
+    p = W.memory_params()
+    b = models.MemoryBasis(p)
+    assert len(b) == 588
+    H = models.memory_csr(p, b).to_scipy()
+    v0 = W.basis_state(len(b), b.index(W.memory_initial_occupation(p)))
+    fwd = krylov.evolve(H, v0, g["t"], g["err_max"], 40)
+    back = krylov.evolve(H, fwd.v, -g["t"], g["err_max"], 40)
+    assert np.linalg.norm(back.v - v0) <= g["printed_requested_bound"]
+    # sector occupations of the two subsystems are conserved by construction; the
+    # dynamics is not trivial
+    assert np.linalg.norm(fwd.v - v0) > 0.1
+
+
+def test_norm1_matches_assembled_matrix():
+    p = W.memory_params(K=3, Kp=3, N0=6, Nm=2, Nc=6.0)
+    b = models.MemoryBasis(p)
+    A = models.memory_csr(p, b).to_scipy()
+    assert abs(models.memory_norm1(p, b) - krylov.norm1(A)) < 1e-12

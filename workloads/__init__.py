@@ -147,6 +147,11 @@ def workload(name: str) -> dict:
         occ = tuple([1] * 10 + [0] * 4)
         return {"name": name, "params": p, "d": bose_dim(14, 10), "v0": ("occupation", occ),
                 "t": 20.0, "m": 50, "tol": 1e-10}
+    if name == "memory_K10":
+        p = memory_params(K=10, Kp=10, N0=100, Nm=5, Nc=100.0)
+        return {"name": name, "params": p, "d": memory_dim(p),
+                "v0": ("occupation", memory_initial_occupation(p)),
+                "t": 10.0, "m": 40, "tol": 1e-7}
     raise KeyError(name)
 
 
@@ -199,3 +204,40 @@ def serve_requests(n: int, seed: int = 5) -> list:
         gap = float(-np.log1p(-u[4 * i + 3]))
         out.append((k, t, tol, 700 + i, gap))
     return out
+
+
+# ---------------------------------------------------------------- the paper's example system
+
+def memory_params(K: int = 4, Kp: int = 4, N0: int = 20, Nm: int = 2, Nc: float = 20.0,
+                  dNc: float = 12.0, em: float | None = None, C0: float = 1.0,
+                  Cm: float = 1.0) -> dict:
+    """Parameters of the paper's example Hamiltonian (Sec. 5, "memory burden" system).
+
+    Two bosonic modes a_0, b_0 holding N0 particles, K + Kp qubit modes holding Nm
+    excitations.  Defaults are the paper's default parameter set (eps_m = sqrt(20),
+    N0 = Nc = 20, dNc = 12, K = K' = 4, C0 = Cm = 1, Nm = 2).  The coupling of qubits
+    p < q (global numbering 1..K+Kp, the second sector after the first) is
+    f = F - 1 if F < 0.5 else F with F = (sqrt(2) (p+1)^3 + sqrt(7) (q+1)^5) mod 1,
+    which is the paper's f_1, f_2 and f_3 with their index offsets; the table lists
+    f for p < q in (p-major, q-minor) order.
+    """
+    Q = K + Kp
+    fs = []
+    for p in range(1, Q + 1):
+        for q in range(p + 1, Q + 1):
+            F = np.mod(np.sqrt(2.0) * (p + 1) ** 3 + np.sqrt(7.0) * (q + 1) ** 5, 1.0)
+            fs.append(F - 1.0 if F < 0.5 else F)
+    return {"model": "memory", "K": K, "Kp": Kp, "N0": N0, "Nm": Nm, "Nc": float(Nc),
+            "dNc": float(dNc), "em": float(np.sqrt(20.0) if em is None else em),
+            "C0": float(C0), "Cm": float(Cm), "f": np.array(fs, dtype=np.float64)}
+
+
+def memory_dim(p: dict) -> int:
+    """(N0 + 1) C(K + K', Nm) states: both sectors conserve their occupation."""
+    return (p["N0"] + 1) * math.comb(p["K"] + p["Kp"], p["Nm"])
+
+
+def memory_initial_occupation(p: dict) -> tuple:
+    """|N0, 0, 1 x Nm, 0, ...>: all bosons in a_0, the first Nm qubits excited."""
+    Q = p["K"] + p["Kp"]
+    return (p["N0"], 0) + tuple([1] * p["Nm"] + [0] * (Q - p["Nm"]))
