@@ -56,7 +56,7 @@ typedef int32_t te_status;
 #define TE_INPUT_IS_CSR      0x4u  /* te_build_csr: rows is a row pointer array of length d+1 */
 
 /* te_stats.flags */
-#define TE_WARN_ROUNDOFF     0x1u  /* d ||H||_1 eps > err_max (eq. numericalError; Sec. 2.4 list) */
+#define TE_WARN_ROUNDOFF     0x1u  /* d ||H||_1 eps exceeded a step's error integral (eq. numericalError, Sec. 2.4) */
 #define TE_WARN_QUAD         0x2u  /* an error integral did not reach quad_rel_tol within quad_max_levels (Sec. 4) */
 #define TE_FLAG_BREAKDOWN    0x4u  /* a lucky breakdown ended a Krylov space early (Sec. 2.4 step 1) */
 
@@ -100,7 +100,8 @@ typedef struct te_options {
 
 /* Per-solve report.  err_bound is the sum of the accepted step errors (the
  * a-posteriori bound on ||v_out - exp(-iHt)v_in|| up to roundoff and the
- * quadrature tolerance).  roundoff_est = d ||H||_1 2^-52 (eq. numericalError). */
+ * quadrature tolerance).  roundoff_est = restarts x d ||H||_1 2^-52: the estimate of
+ * eq. numericalError, once per restart (compared with that restart's error integral). */
 typedef struct te_stats {
     int64_t  restarts;         /* Krylov spaces built */
     int64_t  matvecs;          /* products H v */

@@ -263,6 +263,7 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     ini->smallexp = o.small_exp;
     ini->first = 1;
     ini->m_eff = p->m;
+    ini->min_err_step = INFINITY;
     gauss_legendre_nodes(o.gauss_n, ini->gx, ini->gw);
     const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -286,8 +287,8 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     memset(&S, 0, sizeof(S));
     S.norm_in = h->beta0;
     S.m_used = p->m;
-    S.roundoff_est = (double)d * H->norm1 * 2.220446049250313e-16;
-    if (S.roundoff_est > tol) S.flags |= TE_WARN_ROUNDOFF;
+    // eq. numericalError, compared with each step's error integral (Sec. 2.4)
+    const double per_restart = (double)d * H->norm1 * 2.220446049250313e-16;
     te_status result = TE_OK;
     if (h->status != 0) {
         result = h->status;
@@ -333,6 +334,8 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     }
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     S.restarts = h->restarts;
+    S.roundoff_est = per_restart * (double)h->restarts;
+    if (h->restarts > 0 && per_restart > h->min_err_step) S.flags |= TE_WARN_ROUNDOFF;
     S.matvecs = h->matvecs;
     S.breakdowns = h->breakdowns;
     S.quad_warnings = h->quad_warnings;

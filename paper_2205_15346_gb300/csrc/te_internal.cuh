@@ -74,6 +74,7 @@ struct DevState {
     double spmv_dot;         // te_spmv: Re <x, H x>
     double last_step;
     double last_err;
+    double min_err_step;     // smallest accepted step error (roundoff comparison)
     double scale[TE_M_MAX + 1];   // v_j = scale[j] * u_j (stored vectors are unnormalised)
     double alpha[TE_M_MAX];       // diagonal of H_m
     double beta[TE_M_MAX];        // beta[j] = h_{j+2,j+1} (0-based j); h = beta[m_eff-1]

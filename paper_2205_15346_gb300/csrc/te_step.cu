@@ -662,6 +662,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st, int m
         st->last_m_eff = n;
         st->last_step = tau;
         st->last_err = err;
+        st->min_err_step = fmin(st->min_err_step, err);
         st->done = (st->t_now >= T) ? 1 : 0;
     }
 }

@@ -74,3 +74,26 @@ def test_parity_and_forward_backward_default_parameters(te, ctx):
         assert np.linalg.norm(back.cpu().numpy() - v0) <= g["printed_requested_bound"]
     finally:
         te.te_matrix_free(H)
+
+
+def test_benchmark_system_roundoff_estimate(te, ctx):
+    """Sec. 5: for the benchmark system (t = 10, m = 40, err_max = 1e-7) the roundoff
+    estimate of eq. numericalError is 3.2e-6 and a warning is triggered.  The sum of
+    the per-restart estimates reproduces it up to the restart count, which depends
+    on step-search details (factor 1.5 allowed)."""
+    import torch
+    g = GOLDEN["benchmark"]
+    p = W.memory_params(K=g["K"], Kp=g["Kp"], N0=g["N0"], Nm=g["Nm"], Nc=g["Nc"])
+    H = te.te_build_model(ctx, p)
+    try:
+        d = te.te_matrix_info_get(H)["d"]
+        idx = te.te_model_basis_index(p, W.memory_initial_occupation(p))
+        v0 = torch.zeros(d, dtype=torch.complex128, device="cuda")
+        v0[idx] = 1.0
+        out, st, _ = te.te_evolve(ctx, H, v0, g["t"], g["err_max"], g["m"])
+        assert st["err_bound"] <= g["err_max"]
+        assert st["flags"] & te.TE_WARN_ROUNDOFF
+        ratio = st["roundoff_est"] / g["printed_roundoff_estimate"]
+        assert 1 / 1.5 <= ratio <= 1.5, (st["roundoff_est"], st["restarts"])
+    finally:
+        te.te_matrix_free(H)

@@ -262,7 +262,8 @@ def test_norm1_definition_and_roundoff_estimate():
     A = CASES["xxzdm8"]()
     assert abs(krylov.norm1(A) - np.linalg.norm(A.toarray(), 1)) < 1e-13
     res = krylov.evolve(A, W.random_state(40, 256), 1.0, 1e-8, 20)
-    assert res.roundoff_est == 256 * krylov.norm1(A) * 2.0 ** -52
-    assert res.warn_roundoff == (res.roundoff_est > 1e-8)
+    per = 256 * krylov.norm1(A) * 2.0 ** -52
+    assert res.roundoff_est == res.restarts * per
+    assert res.warn_roundoff == any(per > s[1] for s in res.steps)
     res = krylov.evolve(A, W.random_state(40, 256), 1.0, 1e-14, 20)
     assert res.warn_roundoff
