@@ -264,6 +264,33 @@ te_status te_spmv_noalloc(te_ctx* ctx, const te_matrix* H, const double* x, doub
 te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
                     int32_t m, const te_options* opt, double* v_out, te_stats* st);
 
+/* Largest number of vectors in one block product of te_evolve_batch; larger
+ * batches run in consecutive groups of this size. */
+#define TE_BATCH_MAX 64
+
+/* nvec solves v_out[b] = exp(-i H t) v_in[b] under one H, each to within
+ * err_max = tol (Algorithm 1 applied to every vector; the paper solves one
+ * vector at a time and has no batched form).  The vectors keep separate Krylov
+ * spaces, step sizes, breakdowns and restart counts; what they share is the
+ * product with H, done as one block product per Lanczos step for up to
+ * TE_BATCH_MAX vectors.
+ *   v_in, v_out: nvec complex128 vectors of length d stored one after another
+ *     (vector b at offset 2 b d doubles); device pointers if opt->flags has
+ *     TE_PTR_DEVICE, else host; they may be the same buffer.
+ *   t, tol, m, opt: as for te_evolve, shared by all vectors (opt->reorth must be
+ *     TE_REORTH_NONE; spmv_lanes is ignored).  TE_OPT_PROFILE times the block
+ *     products (spmv_ms is then the group's total, repeated in its vectors).
+ *   st: NULL or nvec entries; status: NULL or nvec entries, each vector's own
+ *     te_status (a failed vector does not stop the others).
+ * Returns TE_OK when every vector succeeded, else the first vector's error, or
+ * a call-level error (TE_ERR_INVALID_ARG, TE_ERR_UNSUPPORTED, TE_ERR_CUDA,
+ * TE_ERR_OOM).  Device memory: (m + 1) d B 16 bytes plus d B 8 bytes for the
+ * group width B (nvec rounded up to a power of two, at most TE_BATCH_MAX), and
+ * 24 bytes per stored entry of H for a cached copy of its values. */
+te_status te_evolve_batch(te_ctx* ctx, const te_matrix* H, int32_t nvec, const double* v_in,
+                          double t, double tol, int32_t m, const te_options* opt, double* v_out,
+                          te_stats* st, int32_t* status);
+
 /* ---- asynchronous requests --------------------------------------------- */
 
 /* Queue a solve with the same meaning as te_evolve.  v_in is copied before the

@@ -53,6 +53,12 @@ void gauss_legendre_nodes(int n, double* x, double* w) {
     }
 }
 
+}  // namespace
+
+void gauss_legendre_table(int n, double* x, double* w) { gauss_legendre_nodes(n, x, w); }
+
+namespace {
+
 void free_plan(Plan* p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -468,7 +474,7 @@ te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
         return TE_ERR_OOM;
     }
     cudaMemset(c->spmv_st, 0, sizeof(DevState));
-    if (step_prepare() != cudaSuccess) {
+    if (step_prepare() != cudaSuccess || block_prepare() != cudaSuccess) {
         te_destroy(c);
         return TE_ERR_CUDA;
     }
@@ -492,6 +498,7 @@ void te_destroy(te_ctx* ctx) {
         if (t.joinable()) t.join();
     for (Plan* p : ctx->plans) free_plan(p);
     ctx->plans.clear();
+    block_plans_release(ctx, 0);
     if (ctx->spmv_st) cudaFree(ctx->spmv_st);
     if (ctx->spmv_st_host) cudaFreeHost(ctx->spmv_st_host);
     if (ctx->spmv_partials) cudaFree(ctx->spmv_partials);
@@ -703,9 +710,11 @@ void te_matrix_free(te_matrix* H) {
             ctx->plans.erase(it, ctx->plans.end());
         }
         for (Plan* p : drop) free_plan(p);
+        block_plans_release(ctx, H->id);
     }
     for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
-                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val})
+                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val,
+                    (void*)H->m3})
         if (q) cudaFree(q);
     delete H;
 }
@@ -774,6 +783,40 @@ te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
                   st, nullptr);
     release_plan(ctx, p);
     return s;
+}
+
+te_status te_evolve_batch(te_ctx* ctx, const te_matrix* H, int32_t nvec, const double* v_in,
+                          double t, double tol, int32_t m, const te_options* opt, double* v_out,
+                          te_stats* st, int32_t* status) {
+    if (!ctx) return TE_ERR_INVALID_ARG;
+    if (nvec < 1) return set_error(ctx, TE_ERR_INVALID_ARG, "nvec must be >= 1");
+    if (!v_in || !v_out) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL vector");
+    te_options o;
+    resolve_options(opt, &o);
+    te_status s = check_solve_args(ctx, H, t, tol, m, o);
+    if (s) return s;
+    if (o.reorth != TE_REORTH_NONE)
+        return set_error(ctx, TE_ERR_UNSUPPORTED, "batched solves use the three-term recurrence only");
+    enter(ctx);
+    if ((s = join_user_stream(ctx))) return s;
+    const int mu = (int)std::min<int64_t>(m, H->d);
+    const bool dev = (o.flags & TE_PTR_DEVICE) != 0;
+    te_status worst = TE_OK;
+    std::string first_err;
+    for (int32_t g = 0; g < nvec; g += TE_BATCH_MAX) {
+        const int n = std::min<int32_t>(TE_BATCH_MAX, nvec - g);
+        const size_t off = (size_t)g * 2 * (size_t)H->d;
+        s = run_block_solve(ctx, H, n, v_in + off, t, tol, mu, o, v_out + off, dev,
+                            st ? st + g : nullptr, status ? status + g : nullptr, ctx->stream);
+        if (s == TE_ERR_CUDA || s == TE_ERR_OOM || s == TE_ERR_INTERNAL) return s;
+        if (s != TE_OK && worst == TE_OK) {
+            worst = s;
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            first_err = ctx->err;
+        }
+    }
+    if (worst != TE_OK) set_error(ctx, worst, first_err);
+    return worst;
 }
 
 // ------------------------------------------------------------------ requests

@@ -68,7 +68,7 @@ struct DevState {
     int32_t stop;            // inner Lanczos loop ended (breakdown)
     int32_t m_eff;
     int32_t breakdown;
-    int32_t pad0;
+    int32_t active;          // K3 took a step in this restart (batched recombination)
     double beta0;            // ||w|| at the start of the restart
     double as_cur;           // alpha_j * scale_j, handed from K1 to K2
     double spmv_dot;         // te_spmv: Re <x, H x>
@@ -105,6 +105,9 @@ struct te_matrix {
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
     int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)
+    // 3M form for the batched product (te_block.cu), built on first use:
+    // m3[k] = a, m3[nnz + k] = b - a, m3[2 nnz + k] = a + b for val[k] = a + ib
+    double* m3 = nullptr;
 };
 
 // One solve's device workspace and captured restart graph.
@@ -191,6 +194,7 @@ cudaError_t launch_reorth_dots(const double2* V, const double2* w, int64_t d, De
 cudaError_t launch_reorth_update(const double2* V, double2* w, int64_t d, DevState* st, int j,
                                  int decide, double* partials, int grid, cudaStream_t s);
 cudaError_t launch_step(DevState* st, int m, cudaStream_t s);
+cudaError_t launch_step_batch(DevState* st, int nvec, int m, cudaStream_t s);
 cudaError_t launch_recombine(double2* V, int64_t d, DevState* st, double* partials, int grid,
                              cudaStream_t s);
 int spmv_grid(int lanes, int64_t d, int num_sms);
@@ -218,6 +222,15 @@ te_status build_memory(te_ctx* ctx, const te_model_desc* desc, te_matrix* H);
 int64_t memory_rank_host(const te_model_desc* desc, const int32_t* occ);
 te_status finish_matrix_stats(te_ctx* ctx, te_matrix* H);
 int64_t bose_rank_host(int K, int N, const int32_t* occ);
+
+// batched solves (te_block.cu)
+cudaError_t block_prepare();
+void block_plans_release(te_ctx* ctx, uint64_t matrix_id);    // matrix_id 0: all of ctx
+te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const double* v_in, double t,
+                          double tol, int m, const te_options& o, double* v_out, bool dev,
+                          te_stats* stats, int32_t* status, cudaStream_t s);
+// Gauss-Legendre nodes and weights on [-1, 1] (te_capi.cu)
+void gauss_legendre_table(int n, double* x, double* w);
 
 te_status set_error(te_ctx* ctx, te_status s, const std::string& msg);
 te_status cuda_error(te_ctx* ctx, cudaError_t e, const char* what);

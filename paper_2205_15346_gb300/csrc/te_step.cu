@@ -395,7 +395,10 @@ __device__ bool ql_eigen(const Layout& L, int n, int* sh_mm, int* sh_nrot, int* 
     return *sh_fail == 0;
 }
 
-__global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st, int mcap) {
+// One CTA per solve: CTA b works on st_base[b] (a batch of independent solves
+// sharing H launches one CTA per vector).
+__global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, int mcap) {
+    DevState* st = st_base + blockIdx.x;
     extern __shared__ double smem[];
     __shared__ double red[33];
     __shared__ int sh_mm, sh_nrot, sh_fail, sh_warn;
@@ -664,6 +667,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st, int m
         st->last_err = err;
         st->min_err_step = fmin(st->min_err_step, err);
         st->done = (st->t_now >= T) ? 1 : 0;
+        st->active = 1;                         // a step was taken: K4 recombines this solve
     }
 }
 
@@ -686,5 +690,10 @@ cudaError_t step_prepare() {
 
 cudaError_t launch_step(DevState* st, int m, cudaStream_t s) {
     k_step<<<1, TE_STEP_THREADS, step_smem_bytes(m), s>>>(st, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(DevState* st, int nvec, int m, cudaStream_t s) {
+    k_step<<<nvec, TE_STEP_THREADS, step_smem_bytes(m), s>>>(st, m);
     return cudaGetLastError();
 }

@@ -102,6 +102,8 @@ _SIGS = {
     "te_spmv_noalloc": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
                               C.POINTER(te_options), _P, C.POINTER(te_stats)]),
+    "te_evolve_batch": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_double, C.c_double, C.c_int32,
+                                    C.POINTER(te_options), _P, _P, _P]),
     "te_submit": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
                               C.POINTER(te_options), C.POINTER(_P)]),
     "te_poll": (C.c_int32, [_P, _P, C.POINTER(te_stats)]),
@@ -364,6 +366,49 @@ def te_evolve(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None
     s = lib().te_evolve(ctx, H, ip, float(t), float(tol), int(m), C.byref(o), op, C.byref(st))
     _check(ctx, s, allow)
     return v_out, st.as_dict(), s
+
+
+def _block_ptr(x, nvec: int, d: int, writable: bool = False):
+    """(pointer, is_device, keepalive) for nvec complex128 vectors of length d, one after another."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.complex128 or x.numel() != nvec * d or not x.is_contiguous():
+            raise ValueError("expected a contiguous complex128 tensor of nvec x d elements")
+        return C.c_void_p(x.data_ptr()), x.is_cuda, x
+    a = np.asarray(x)
+    if a.dtype != np.complex128 or a.size != nvec * d or not a.flags["C_CONTIGUOUS"]:
+        if writable:
+            raise ValueError("output must be a contiguous complex128 array of nvec x d elements")
+        a = np.ascontiguousarray(a, dtype=np.complex128).reshape(-1)
+        if a.size != nvec * d:
+            raise ValueError("block size does not match nvec x d")
+    return C.c_void_p(a.ctypes.data), False, a
+
+
+def te_evolve_batch(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None,
+                    v_out=None, allow=(TE_OK,)):
+    """exp(-iHt) applied to every row of v_in (shape (nvec, d)); returns
+    (v_out, list of stats dicts, list of per-vector statuses, call status)."""
+    d = te_matrix_info_get(H)["d"]
+    nvec = int(v_in.shape[0])
+    ip, idev, ik = _block_ptr(v_in, nvec, d)
+    if v_out is None:
+        if idev:
+            import torch
+            v_out = torch.empty_like(v_in)
+        else:
+            v_out = np.empty((nvec, d), dtype=np.complex128)
+    op, odev, ok = _block_ptr(v_out, nvec, d, writable=True)
+    if idev != odev:
+        raise ValueError("v_in and v_out must both be host or both be device buffers")
+    o = te_options.from_buffer_copy(opt if opt is not None else te_default_options())
+    o.flags = (o.flags & ~TE_PTR_DEVICE) | (TE_PTR_DEVICE if idev else 0)
+    sts = (te_stats * nvec)()
+    stat = (C.c_int32 * nvec)()
+    s = lib().te_evolve_batch(ctx, H, nvec, ip, float(t), float(tol), int(m), C.byref(o), op,
+                              C.cast(sts, C.c_void_p), C.cast(stat, C.c_void_p))
+    _check(ctx, s, allow)
+    return v_out, [x.as_dict() for x in sts], [int(x) for x in stat], s
 
 
 def te_submit(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None):

@@ -147,12 +147,22 @@ def workload(name: str) -> dict:
         occ = tuple([1] * 10 + [0] * 4)
         return {"name": name, "params": p, "d": bose_dim(14, 10), "v0": ("occupation", occ),
                 "t": 20.0, "m": 50, "tol": 1e-10}
+    if name == "batch_xxzdm_L20_x64":
+        # 64 random initial vectors under the Hamiltonian of xxzdm_L20
+        p = xxzdm_params(20, seed=3)
+        return {"name": name, "params": p, "d": 1 << 20, "nvec": 64,
+                "v0_seeds": list(range(301, 365)), "t": 50.0, "m": 40, "tol": 1e-8}
     if name == "memory_K10":
         p = memory_params(K=10, Kp=10, N0=100, Nm=5, Nc=100.0)
         return {"name": name, "params": p, "d": memory_dim(p),
                 "v0": ("occupation", memory_initial_occupation(p)),
                 "t": 10.0, "m": 40, "tol": 1e-7}
     raise KeyError(name)
+
+
+def initial_block(seeds, d: int) -> np.ndarray:
+    """len(seeds) x d block of normalised random states, one row per seed."""
+    return np.stack([random_state(s, d) for s in seeds])
 
 
 def initial_vector(spec, d: int, index_of=None) -> np.ndarray:
