@@ -311,11 +311,16 @@ def run_ours(args):
     e2e_value = job_throughput(args.steps, world, e2e_elapsed)
 
     # roofline of the dominant kernel (K1, fused SpMV + alpha partials), live CUDA-event times.
-    # K1 is bound by the FP64 pipe: 8 FLOP per stored complex entry (4 DFMA) plus 10 per
-    # row (scale, three-term subtraction, alpha partial); HBM bytes are reported beside it.
+    # K1 is bound by the FP64 pipe.  It executes 3 DFMA (6 FLOP) per stored complex
+    # entry (the three-multiplication complex product) plus 12 FLOP per row (combine,
+    # scale, three-term subtraction, alpha partial); the plain complex product would
+    # take 8 FLOP per entry.  Bytes: a, (b-a, a+b) and the column per entry; x, x+y,
+    # u_{j-1} read and y written per row; slice offsets.  HBM is reported beside it.
     nnz = info["nnz"]
-    k1_bytes = 20 * nnz + 4 * (d + 1) + 48 * d
-    k1_flops = 8 * nnz + 10 * d
+    nslices = (d + 31) // 32
+    k1_bytes = 28 * nnz + 4 * (nslices + 1) + 56 * d
+    k1_flops = 6 * nnz + 12 * d
+    k1_flops_complex = 8 * nnz + 12 * d
     spmv_ms = sum(s["spmv_ms"] for s in stats)
     spmv_n = sum(s["spmv_launches"] for s in stats)
     k1_avg_s = spmv_ms / spmv_n / 1000.0
@@ -345,6 +350,7 @@ def run_ours(args):
                          "traffic": recorded_traffic(),
                          "kernel": "k_spmv_sell (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)",
                          "flops_per_launch": k1_flops, "bytes_per_launch": k1_bytes,
+                         "complex_equivalent_tflops": k1_flops_complex / k1_avg_s / 1e12,
                          "avg_launch_ms": 1000.0 * k1_avg_s,
                          "peak_kind": ("derived FP64 pipe peak: 152 SMs x 2 DFMA lanes x 2 FLOP x "
                                        f"{sm_max_mhz:.0f} MHz"),

@@ -65,6 +65,7 @@ void free_plan(Plan* p) {
     if (p->graph) cudaGraphDestroy(p->graph);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     if (p->V) cudaFree(p->V);
+    if (p->S) cudaFree(p->S);
     if (p->st) cudaFree(p->st);
     if (p->partials) cudaFree(p->partials);
     if (p->partials_r) cudaFree(p->partials_r);
@@ -74,8 +75,8 @@ void free_plan(Plan* p) {
 }
 
 size_t plan_bytes(int64_t d, int m, int reorth, int max_grid) {
-    size_t b = sizeof(double2) * (size_t)(m + 1) * (size_t)d + sizeof(DevState) +
-               sizeof(double) * (size_t)max_grid;
+    size_t b = sizeof(double2) * (size_t)(m + 1) * (size_t)d + sizeof(double) * (size_t)d +
+               sizeof(DevState) + sizeof(double) * (size_t)max_grid;
     if (reorth) b += sizeof(double) * (size_t)max_grid * TE_M_MAX * 2;
     return b;
 }
@@ -96,24 +97,26 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         if (e == cudaSuccess)
             e = p->lanes ? launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
                                                p->grid_k1, s)
-                         : launch_spmv_sell(H, x, xprev, y, p->st, j, 0, p->partials, s);
+                         : launch_spmv_sell(H, x, p->S, xprev, y, p->st, j, 0, p->partials, s);
         if (p->profile && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
         if (p->reorth) {
-            e = launch_orth_norm(y, x, d, p->st, j, 1, 0, p->partials, p->grid_stream, s);
+            e = launch_orth_norm(y, p->S, x, d, p->st, j, 1, 0, p->partials, p->grid_stream, s);
             for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
                 e = launch_reorth_dots(p->V, y, d, p->st, j, p->partials_r, p->grid_reorth, s);
                 if (e == cudaSuccess)
-                    e = launch_reorth_update(p->V, y, d, p->st, j, pass == 1, p->partials,
+                    e = launch_reorth_update(p->V, y, p->S, d, p->st, j, pass == 1, p->partials,
                                              p->grid_stream, s);
             }
         } else {
-            e = launch_orth_norm(y, x, d, p->st, j, j + 1 < m, 1, p->partials, p->grid_stream, s);
+            e = launch_orth_norm(y, p->S, x, d, p->st, j, j + 1 < m, 1, p->partials,
+                                 p->grid_stream, s);
         }
     }
     if (e == cudaSuccess) e = launch_step(p->st, m, s);
-    if (e == cudaSuccess) e = launch_recombine(p->V, d, p->st, p->partials, p->grid_stream, s);
+    if (e == cudaSuccess)
+        e = launch_recombine(p->V, p->S, d, p->st, p->partials, p->grid_stream, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     cudaGraph_t g = nullptr;
@@ -146,6 +149,7 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
                                                 lanes ? 0 : sell_partials(H));
     p->bytes = plan_bytes(H->d, m, reorth, max_grid);
     cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
+    if (e == cudaSuccess && lanes == 0) e = cudaMalloc(&p->S, sizeof(double) * (size_t)H->d);
     if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * (size_t)max_grid);
     if (e == cudaSuccess && reorth)
@@ -280,12 +284,12 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     if (!sell) {
         TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->V, v_in, sizeof(double2) * d, kin, s));
     } else if (dev) {
-        TE_CUDA_TRY(ctx, launch_gather((const double2*)v_in, H->perm, d, p->V, ctx->num_sms, s));
+        TE_CUDA_TRY(ctx, launch_gather((const double2*)v_in, H->perm, d, p->V, nullptr, ctx->num_sms, s));
     } else {
         TE_CUDA_TRY(ctx, cudaMemcpyAsync(stage, v_in, sizeof(double2) * d, kin, s));
-        TE_CUDA_TRY(ctx, launch_gather(stage, H->perm, d, p->V, ctx->num_sms, s));
+        TE_CUDA_TRY(ctx, launch_gather(stage, H->perm, d, p->V, nullptr, ctx->num_sms, s));
     }
-    TE_CUDA_TRY(ctx, launch_init_norm(p->V, d, p->st, p->partials, p->grid_stream, s));
+    TE_CUDA_TRY(ctx, launch_init_norm(p->V, p->S, d, p->st, p->partials, p->grid_stream, s));
     TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const DevState* h = p->st_host;
@@ -333,9 +337,9 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     if (!sell) {
         TE_CUDA_TRY(ctx, cudaMemcpyAsync(v_out, p->V, sizeof(double2) * d, kout, s));
     } else if (dev) {
-        TE_CUDA_TRY(ctx, launch_gather(p->V, H->iperm, d, (double2*)v_out, ctx->num_sms, s));
+        TE_CUDA_TRY(ctx, launch_gather(p->V, H->iperm, d, (double2*)v_out, nullptr, ctx->num_sms, s));
     } else {
-        TE_CUDA_TRY(ctx, launch_gather(p->V, H->iperm, d, stage, ctx->num_sms, s));
+        TE_CUDA_TRY(ctx, launch_gather(p->V, H->iperm, d, stage, nullptr, ctx->num_sms, s));
         TE_CUDA_TRY(ctx, cudaMemcpyAsync(v_out, stage, sizeof(double2) * d, kout, s));
     }
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -713,7 +717,7 @@ void te_matrix_free(te_matrix* H) {
         block_plans_release(ctx, H->id);
     }
     for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
-                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_val,
+                    (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_a, (void*)H->sell_pq,
                     (void*)H->m3})
         if (q) cudaFree(q);
     delete H;
@@ -733,24 +737,25 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
     // the product runs in the length-sorted basis of the SELL form: x enters
     // through perm, y leaves through iperm
     double2 *xs = nullptr, *ys = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&xs, sizeof(double2) * 2 * (size_t)d +
+    TE_CUDA_TRY(ctx, cudaMalloc(&xs, sizeof(double2) * 2 * (size_t)d + sizeof(double) * (size_t)d +
                                          sizeof(double) * (size_t)sell_partials(H)));
     ys = xs + d;
-    double* parts = reinterpret_cast<double*>(ys + d);
+    double* xsum = reinterpret_cast<double*>(ys + d);
+    double* parts = xsum + d;
     cudaError_t e = cudaSuccess;
     if (dev) {
-        e = launch_gather((const double2*)x, H->perm, d, xs, ctx->num_sms, s);
+        e = launch_gather((const double2*)x, H->perm, d, xs, xsum, ctx->num_sms, s);
     } else {
         e = cudaMemcpyAsync(ys, x, sizeof(double2) * d, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = launch_gather(ys, H->perm, d, xs, ctx->num_sms, s);
+        if (e == cudaSuccess) e = launch_gather(ys, H->perm, d, xs, xsum, ctx->num_sms, s);
     }
     if (e == cudaSuccess)
-        e = launch_spmv_sell(H, xs, nullptr, ys, ctx->spmv_st, 0, 1, parts, s);
+        e = launch_spmv_sell(H, xs, xsum, nullptr, ys, ctx->spmv_st, 0, 1, parts, s);
     if (e == cudaSuccess) {
         if (dev) {
-            e = launch_gather(ys, H->iperm, d, (double2*)y, ctx->num_sms, s);
+            e = launch_gather(ys, H->iperm, d, (double2*)y, nullptr, ctx->num_sms, s);
         } else {
-            e = launch_gather(ys, H->iperm, d, xs, ctx->num_sms, s);
+            e = launch_gather(ys, H->iperm, d, xs, nullptr, ctx->num_sms, s);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(y, xs, sizeof(double2) * d, cudaMemcpyDeviceToHost, s);
         }

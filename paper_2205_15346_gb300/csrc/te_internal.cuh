@@ -101,7 +101,8 @@ struct te_matrix {
     int32_t* iperm = nullptr;    // old row -> new index
     int32_t* sell_off = nullptr; // slice offsets, nslices + 1
     int32_t* sell_col = nullptr;
-    double2* sell_val = nullptr;
+    double* sell_a = nullptr;    // Re h per stored entry
+    double2* sell_pq = nullptr;  // (Im h - Re h, Re h + Im h) per stored entry (3M product)
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
     int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)
@@ -120,6 +121,7 @@ struct Plan {
     int lanes = 0;                   // 0: SELL kernel in the permuted basis; > 0: CSR kernel
     int64_t d = 0;
     double2* V = nullptr;            // (m + 1) columns of length d, column-major
+    double* S = nullptr;             // Re + Im of the Lanczos vector the next SpMV reads (SELL)
     DevState* st = nullptr;          // device
     DevState* st_host = nullptr;     // pinned: written by the graph's last node
     DevState* st_init = nullptr;     // pinned: source of the per-solve initial state
@@ -182,21 +184,24 @@ struct te_ctx {
 // ---- host launchers (kernels live in te_lanczos.cu, te_step.cu, te_build.cu)
 
 int spmv_lanes_for(double avg_row_nnz);
-cudaError_t launch_init_norm(const double2* v, int64_t d, DevState* st, double* partials,
-                             int grid, cudaStream_t s);
+// S (may be null) receives Re v + Im v of every vector these kernels write,
+// for the three-multiplication product of the SELL kernel.
+cudaError_t launch_init_norm(const double2* v, double* S, int64_t d, DevState* st,
+                             double* partials, int grid, cudaStream_t s);
 cudaError_t launch_spmv_lanczos(const te_matrix* H, int lanes, const double2* x,
                                 const double2* xprev, double2* y, DevState* st, int j,
                                 int mode, double* partials, int grid, cudaStream_t s);
-cudaError_t launch_orth_norm(double2* w, const double2* u, int64_t d, DevState* st, int j,
-                             int write, int decide, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_orth_norm(double2* w, double* S, const double2* u, int64_t d, DevState* st,
+                             int j, int write, int decide, double* partials, int grid,
+                             cudaStream_t s);
 cudaError_t launch_reorth_dots(const double2* V, const double2* w, int64_t d, DevState* st,
                                int j, double* partials, int grid, cudaStream_t s);
-cudaError_t launch_reorth_update(const double2* V, double2* w, int64_t d, DevState* st, int j,
-                                 int decide, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_reorth_update(const double2* V, double2* w, double* S, int64_t d, DevState* st,
+                                 int j, int decide, double* partials, int grid, cudaStream_t s);
 cudaError_t launch_step(DevState* st, int m, cudaStream_t s);
 cudaError_t launch_step_batch(DevState* st, int nvec, int m, cudaStream_t s);
-cudaError_t launch_recombine(double2* V, int64_t d, DevState* st, double* partials, int grid,
-                             cudaStream_t s);
+cudaError_t launch_recombine(double2* V, double* S, int64_t d, DevState* st, double* partials,
+                             int grid, cudaStream_t s);
 int spmv_grid(int lanes, int64_t d, int num_sms);
 int occupancy_grid_spmv(int lanes, int num_sms);
 int step_smem_bytes(int m);
@@ -206,11 +211,11 @@ cudaError_t step_prepare();
 te_status build_sell(te_ctx* ctx, te_matrix* H);
 int sell_grid(int64_t nslices, int num_sms);
 int64_t sell_partials(const te_matrix* H);
-cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
-                             double2* y, DevState* st, int j, int mode, double* partials,
-                             cudaStream_t s);
+cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
+                             const double2* xprev, double2* y, DevState* st, int j, int mode,
+                             double* partials, cudaStream_t s);
 cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
-                          int num_sms, cudaStream_t s);
+                          double* dsum, int num_sms, cudaStream_t s);
 te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowptr, int64_t* nnz,
                       cudaStream_t s);
 

@@ -66,7 +66,8 @@ __device__ __forceinline__ bool halted(const DevState* st) {
 
 // ---------------------------------------------------------------- K0
 
-__global__ void __launch_bounds__(TE_BLOCK) k_init_norm(const double2* __restrict__ v, int64_t d,
+__global__ void __launch_bounds__(TE_BLOCK) k_init_norm(const double2* __restrict__ v,
+                                                        double* __restrict__ S, int64_t d,
                                                         DevState* st, double* partials) {
     __shared__ double sh[32];
     double acc = 0.0;
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_init_norm(const double2* __restric
         double2 a = v[i];
         finite &= isfinite(a.x) && isfinite(a.y);
         acc += a.x * a.x + a.y * a.y;
+        if (S) S[i] = a.x + a.y;
     }
     if (!finite) acc = __longlong_as_double(0x7ff8000000000000LL);   // NaN marks it
     double s = block_sum(acc, sh);
@@ -210,6 +212,7 @@ __device__ __forceinline__ void lanczos_decide(DevState* st, int j, double nrm) 
 }
 
 __global__ void __launch_bounds__(TE_BLOCK) k_orth_norm(double2* __restrict__ w,
+                                                        double* __restrict__ S,
                                                         const double2* __restrict__ u, int64_t d,
                                                         DevState* st, int j, int write,
                                                         int decide, double* partials) {
@@ -231,7 +234,10 @@ __global__ void __launch_bounds__(TE_BLOCK) k_orth_norm(double2* __restrict__ w,
         for (int q = 0; q < 4; ++q) {
             yv[q].x = fma(-as, uv[q].x, yv[q].x);
             yv[q].y = fma(-as, uv[q].y, yv[q].y);
-            if (write) w[i + q * stride] = yv[q];
+            if (write) {
+                w[i + q * stride] = yv[q];
+                if (S) S[i + q * stride] = yv[q].x + yv[q].y;
+            }
             acc = fma(yv[q].x, yv[q].x, acc);
             acc = fma(yv[q].y, yv[q].y, acc);
         }
@@ -241,7 +247,10 @@ __global__ void __launch_bounds__(TE_BLOCK) k_orth_norm(double2* __restrict__ w,
         const double2 u0 = __ldg(u + i);
         y0.x = fma(-as, u0.x, y0.x);
         y0.y = fma(-as, u0.y, y0.y);
-        if (write) w[i] = y0;
+        if (write) {
+            w[i] = y0;
+            if (S) S[i] = y0.x + y0.y;
+        }
         acc = fma(y0.x, y0.x, acc);
         acc = fma(y0.y, y0.y, acc);
     }
@@ -306,7 +315,8 @@ __global__ void __launch_bounds__(TE_BLOCK) k_reorth_dots(const double2* __restr
 
 // w -= sum_k rcoef[k] u_k; with decide, also ||w|| and the breakdown test.
 __global__ void __launch_bounds__(TE_BLOCK) k_reorth_update(const double2* __restrict__ V,
-                                                            double2* __restrict__ w, int64_t d,
+                                                            double2* __restrict__ w,
+                                                            double* __restrict__ S, int64_t d,
                                                             DevState* st, int j, int decide,
                                                             double* partials) {
     __shared__ double sh[32];
@@ -325,6 +335,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_reorth_update(const double2* __res
             r.y -= c[k].x * a.y + c[k].y * a.x;
         }
         w[i] = r;
+        if (S) S[i] = r.x + r.y;
         acc += r.x * r.x + r.y * r.y;
     }
     if (!decide) return;
@@ -342,7 +353,8 @@ __global__ void __launch_bounds__(TE_BLOCK) k_reorth_update(const double2* __res
 
 // w = sum_{k < m_eff} coef[k] u_k into column 0, then ||w|| for the next restart
 // (Algorithm 1 step 3; v_1 of the next Krylov space is w / ||w||).
-__global__ void __launch_bounds__(TE_BLOCK) k_recombine(double2* __restrict__ V, int64_t d,
+__global__ void __launch_bounds__(TE_BLOCK) k_recombine(double2* __restrict__ V,
+                                                        double* __restrict__ S, int64_t d,
                                                         DevState* st, double* partials) {
     __shared__ double sh[32];
     __shared__ double2 c[TE_M_MAX];
@@ -375,6 +387,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_recombine(double2* __restrict__ V,
             im = fma(c[k].y, a.x, im);
         }
         V[i] = make_double2(re, im);
+        if (S) S[i] = re + im;
         acc += re * re + im * im;
     }
     const double s = block_sum(acc, sh);
@@ -430,9 +443,9 @@ int spmv_grid(int lanes, int64_t d, int num_sms) {
     return (int)(need < full ? (need > 0 ? need : 1) : full);
 }
 
-cudaError_t launch_init_norm(const double2* v, int64_t d, DevState* st, double* partials,
-                             int grid, cudaStream_t s) {
-    k_init_norm<<<grid, TE_BLOCK, 0, s>>>(v, d, st, partials);
+cudaError_t launch_init_norm(const double2* v, double* S, int64_t d, DevState* st,
+                             double* partials, int grid, cudaStream_t s) {
+    k_init_norm<<<grid, TE_BLOCK, 0, s>>>(v, S, d, st, partials);
     return cudaGetLastError();
 }
 
@@ -454,9 +467,10 @@ cudaError_t launch_spmv_lanczos(const te_matrix* H, int lanes, const double2* x,
     return cudaGetLastError();
 }
 
-cudaError_t launch_orth_norm(double2* w, const double2* u, int64_t d, DevState* st, int j,
-                             int write, int decide, double* partials, int grid, cudaStream_t s) {
-    k_orth_norm<<<grid, TE_BLOCK, 0, s>>>(w, u, d, st, j, write, decide, partials);
+cudaError_t launch_orth_norm(double2* w, double* S, const double2* u, int64_t d, DevState* st,
+                             int j, int write, int decide, double* partials, int grid,
+                             cudaStream_t s) {
+    k_orth_norm<<<grid, TE_BLOCK, 0, s>>>(w, S, u, d, st, j, write, decide, partials);
     return cudaGetLastError();
 }
 
@@ -466,14 +480,14 @@ cudaError_t launch_reorth_dots(const double2* V, const double2* w, int64_t d, De
     return cudaGetLastError();
 }
 
-cudaError_t launch_reorth_update(const double2* V, double2* w, int64_t d, DevState* st, int j,
-                                 int decide, double* partials, int grid, cudaStream_t s) {
-    k_reorth_update<<<grid, TE_BLOCK, 0, s>>>(V, w, d, st, j, decide, partials);
+cudaError_t launch_reorth_update(const double2* V, double2* w, double* S, int64_t d, DevState* st,
+                                 int j, int decide, double* partials, int grid, cudaStream_t s) {
+    k_reorth_update<<<grid, TE_BLOCK, 0, s>>>(V, w, S, d, st, j, decide, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_recombine(double2* V, int64_t d, DevState* st, double* partials, int grid,
-                             cudaStream_t s) {
-    k_recombine<<<grid, TE_BLOCK, 0, s>>>(V, d, st, partials);
+cudaError_t launch_recombine(double2* V, double* S, int64_t d, DevState* st, double* partials,
+                             int grid, cudaStream_t s) {
+    k_recombine<<<grid, TE_BLOCK, 0, s>>>(V, S, d, st, partials);
     return cudaGetLastError();
 }

@@ -12,8 +12,19 @@
 // perm[i], columns are renumbered through iperm, and the solver works on
 // permuted vectors (copied in and out once per solve).  Entries of slice s
 // are stored lane-interleaved: entry k of lane l sits at off[s] + 32 k + l, so
-// each warp load is 32 consecutive 16-byte values.  Padding entries hold 0 and
-// point at the lane's own row.
+// each warp load is 32 consecutive values.  Padding entries hold 0 and point at
+// the lane's own row.
+//
+// Each complex multiply-add costs three DFMA instead of four: for an entry
+// h = a + ib and a vector element x + iy,
+//     Re(h x) = a (x + y) - (a + b) y,   Im(h x) = a (x + y) + (b - a) x
+// (Gauss's three-multiplication complex product; normwise stable, Higham, SIAM
+// J. Matrix Anal. Appl. 13 (1992) 681).  The matrix keeps a and the pair
+// (b - a, a + b) per entry, and the product reads the sums s = x + y of the
+// vector from a companion array that the kernels writing Lanczos vectors fill.
+// The three sums are accumulated separately over the row and combined at its
+// end.  The gathers this adds go to the load/store path, which this kernel
+// leaves mostly idle.
 #include <algorithm>
 #include <vector>
 
@@ -77,7 +88,7 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
                             const double2* __restrict__ val, const int32_t* __restrict__ perm,
                             const int32_t* __restrict__ iperm, const int32_t* __restrict__ off,
                             int64_t d, int64_t nslices, int32_t* __restrict__ scol,
-                            double2* __restrict__ sval) {
+                            double* __restrict__ sa, double2* __restrict__ spq) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nslices * 32) return;
     const int64_t s = i >> 5;
@@ -94,35 +105,33 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
     for (int k = 0; k < w; ++k) {
         const int64_t p = o + 32ll * k + lane;
         if (k < len) {
+            const double2 v = val[b + k];
             scol[p] = iperm[col[b + k]];
-            sval[p] = val[b + k];
+            sa[p] = v.x;                                   // a
+            spq[p] = make_double2(v.y - v.x, v.x + v.y);   // (b - a, a + b)
         } else {
             scol[p] = self;
-            sval[p] = make_double2(0.0, 0.0);
+            sa[p] = 0.0;
+            spq[p] = make_double2(0.0, 0.0);
         }
     }
 }
 
 // ---------------------------------------------------------------- SpMV
 
-__device__ __forceinline__ void cmac(double& re, double& im, const double2 a, const double2 x) {
-    re = fma(a.x, x.x, re);
-    re = fma(-a.y, x.y, re);
-    im = fma(a.x, x.y, im);
-    im = fma(a.y, x.x, im);
-}
-
 // mode 0: Lanczos step j (y = sign scale[j] H u_j - beta[j-1] scale[j-1] u_{j-1},
-// partial Re<u_j, y>, matvec count); mode 1: y = H x and Re<x, y>.
+// partial Re<u_j, y>, matvec count); mode 1: y = H x and Re<x, y>.  xs[i] must
+// hold Re x_i + Im x_i.
 //
 // Work is handed out in chunks of kChunk slices through an atomic counter, so
 // SMs that run slower (far-die L2 traffic, other streams) simply take fewer
 // chunks.  Each chunk stores its own partial of Re<x, y>; the last block adds
 // the chunk partials in chunk order, so the result does not depend on which
 // warp took which chunk.
-__global__ void __launch_bounds__(TE_BLOCK, 6) k_spmv_sell(
+__global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sell(
     const int32_t* __restrict__ off, const int32_t* __restrict__ col,
-    const double2* __restrict__ val, const double2* __restrict__ x,
+    const double* __restrict__ va, const double2* __restrict__ vpq,
+    const double2* __restrict__ x, const double* __restrict__ xs,
     const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
     DevState* st, int j, int mode, double* partials) {
     __shared__ double sh[32];
@@ -146,32 +155,38 @@ __global__ void __launch_bounds__(TE_BLOCK, 6) k_spmv_sell(
         for (int64_t s = (int64_t)c * kChunk; s < s1; ++s) {
             const int32_t o = __ldg(off + s);
             const int w = (__ldg(off + s + 1) - o) >> 5;
-            const double2* vp = val + o + lane;
+            const double* ap = va + o + lane;
+            const double2* qp = vpq + o + lane;
             const int32_t* cp = col + o + lane;
-            // one accumulator pair: the FP64 pipe, not the FMA latency, is the limit,
-            // and fewer registers keep six blocks resident per SM
-            double re = 0.0, im = 0.0;
+            // k1 = sum a s, k2 = sum (b - a) x, k3 = sum (a + b) y
+            double k1 = 0.0, k2 = 0.0, k3 = 0.0;
             int k = 0;
-            for (; k + 4 <= w; k += 4) {
-                const double2 a0 = __ldcs(vp + 32 * k), a1 = __ldcs(vp + 32 * (k + 1));
-                const double2 a2 = __ldcs(vp + 32 * (k + 2)), a3 = __ldcs(vp + 32 * (k + 3));
+            for (; k + 2 <= w; k += 2) {
+                const double a0 = __ldcs(ap + 32 * k), a1 = __ldcs(ap + 32 * (k + 1));
+                const double2 q0 = __ldcs(qp + 32 * k), q1 = __ldcs(qp + 32 * (k + 1));
                 const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
-                const int c2 = __ldcs(cp + 32 * (k + 2)), c3 = __ldcs(cp + 32 * (k + 3));
                 const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-                const double2 x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-                cmac(re, im, a0, x0);
-                cmac(re, im, a1, x1);
-                cmac(re, im, a2, x2);
-                cmac(re, im, a3, x3);
+                const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
+                k1 = fma(a0, z0, k1);
+                k2 = fma(q0.x, x0.x, k2);
+                k3 = fma(q0.y, x0.y, k3);
+                k1 = fma(a1, z1, k1);
+                k2 = fma(q1.x, x1.x, k2);
+                k3 = fma(q1.y, x1.y, k3);
             }
-            for (; k < w; ++k) {
-                const double2 a0 = __ldcs(vp + 32 * k);
-                const double2 x0 = __ldg(x + __ldcs(cp + 32 * k));
-                cmac(re, im, a0, x0);
+            if (k < w) {
+                const double a0 = __ldcs(ap + 32 * k);
+                const double2 q0 = __ldcs(qp + 32 * k);
+                const int c0 = __ldcs(cp + 32 * k);
+                const double2 x0 = __ldg(x + c0);
+                const double z0 = __ldg(xs + c0);
+                k1 = fma(a0, z0, k1);
+                k2 = fma(q0.x, x0.x, k2);
+                k3 = fma(q0.y, x0.y, k3);
             }
             const int64_t row = s * 32 + lane;
             if (row < d) {
-                double2 out = make_double2(cx * re, cx * im);
+                double2 out = make_double2(cx * (k1 - k3), cx * (k1 + k2));
                 if (bp != 0.0) {
                     const double2 p = __ldcs(xprev + row);
                     out.x = fma(-bp, p.x, out.x);
@@ -215,12 +230,16 @@ __global__ void __launch_bounds__(TE_BLOCK, 6) k_spmv_sell(
     }
 }
 
-// dst[i] = src[map[i]]  (map = perm: old -> new order; map = iperm: back)
+// dst[i] = src[map[i]]  (map = perm: old -> new order; map = iperm: back);
+// with dsum, also dsum[i] = Re dst[i] + Im dst[i] for the product's 3M form.
 __global__ void k_gather(const double2* __restrict__ src, const int32_t* __restrict__ map,
-                         int64_t d, double2* __restrict__ dst) {
+                         int64_t d, double2* __restrict__ dst, double* __restrict__ dsum) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
-         i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[map[i]];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[map[i]];
+        dst[i] = v;
+        if (dsum) dsum[i] = v.x + v.y;
+    }
 }
 
 }  // namespace
@@ -251,10 +270,11 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
     H->nslices = nslices;
     H->sell_nnz = total;
     TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_col, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1)));
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_val, sizeof(double2) * (size_t)std::max<int64_t>(total, 1)));
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_a, sizeof(double) * (size_t)std::max<int64_t>(total, 1)));
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_pq, sizeof(double2) * (size_t)std::max<int64_t>(total, 1)));
     k_sell_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
         H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,
-        H->sell_val);
+        H->sell_a, H->sell_pq);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     H->sell_grid = sell_grid(nslices, ctx->num_sms);
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -270,20 +290,22 @@ int sell_grid(int64_t nslices, int num_sms) {
     return (int)std::max<int64_t>(1, std::min(need, full));
 }
 
-// partials must hold sell_partials(H) doubles (one per chunk of slices).
-cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double2* xprev,
-                             double2* y, DevState* st, int j, int mode, double* partials,
-                             cudaStream_t s) {
-    k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_val, x, xprev,
-                                                 y, H->d, H->nslices, st, j, mode, partials);
+// partials must hold sell_partials(H) doubles (one per chunk of slices); xs holds
+// Re x + Im x.
+cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
+                             const double2* xprev, double2* y, DevState* st, int j, int mode,
+                             double* partials, cudaStream_t s) {
+    k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_a, H->sell_pq,
+                                                 x, xs, xprev, y, H->d, H->nslices, st, j, mode,
+                                                 partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
-                          int num_sms, cudaStream_t s) {
+                          double* dsum, int num_sms, cudaStream_t s) {
     const int64_t want = (d + TE_BLOCK - 1) / TE_BLOCK;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * 8));
-    k_gather<<<grid, TE_BLOCK, 0, s>>>(src, map, d, dst);
+    k_gather<<<grid, TE_BLOCK, 0, s>>>(src, map, d, dst, dsum);
     return cudaGetLastError();
 }
 
