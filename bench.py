@@ -37,7 +37,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "exp(-iHt)v solves/s and p50/p99 latency at bound 1e-8; SpMV HBM GB/s vs peak"
 WORKLOAD = "xxzdm_L22"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_spmv_sell_xxzdm_L22.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_spmv_sellv_xxzdm_L22.md")
 K1_SOURCE = os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", "te_sell.cu")
 # FP64 issue rate of GB300: 2 DFMA lanes per SM per cycle (ncu reports a sustained
 # peak of 304 DFMA thread-instructions per cycle over the 152 SMs)
@@ -318,9 +318,18 @@ def run_ours(args):
     # u_{j-1} read and y written per row; slice offsets.  HBM is reported beside it.
     nnz = info["nnz"]
     nslices = (d + 31) // 32
-    k1_bytes = 28 * nnz + 4 * (nslices + 1) + 56 * d
-    k1_flops = 6 * nnz + 12 * d
-    k1_flops_complex = 8 * nnz + 12 * d
+    if info["sell_dict"] > 0:
+        # value-indexed copy: column + 16-bit table index per off-diagonal entry, the
+        # real diagonal per row (the model builders store every diagonal entry, so
+        # there are nnz - d off-diagonal entries); diagonal term 2 DFMA per row
+        off = nnz - d
+        k1_bytes = 6 * off + 8 * d + 4 * (nslices + 1) + 56 * d + 24 * info["sell_dict"]
+        k1_flops = 6 * off + 16 * d
+        k1_flops_complex = 8 * off + 16 * d
+    else:
+        k1_bytes = 28 * nnz + 4 * (nslices + 1) + 56 * d
+        k1_flops = 6 * nnz + 12 * d
+        k1_flops_complex = 8 * nnz + 12 * d
     spmv_ms = sum(s["spmv_ms"] for s in stats)
     spmv_n = sum(s["spmv_launches"] for s in stats)
     k1_avg_s = spmv_ms / spmv_n / 1000.0
@@ -348,7 +357,9 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
                          "traffic": recorded_traffic(),
-                         "kernel": "k_spmv_sell (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)",
+                         "kernel": (("k_spmv_sellv" if info["sell_dict"] > 0 else "k_spmv_sell") +
+                                    " (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)"),
+                         "value_table": info["sell_dict"],
                          "flops_per_launch": k1_flops, "bytes_per_launch": k1_bytes,
                          "complex_equivalent_tflops": k1_flops_complex / k1_avg_s / 1e12,
                          "avg_launch_ms": 1000.0 * k1_avg_s,

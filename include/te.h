@@ -129,6 +129,10 @@ typedef struct te_matrix_info {
     int32_t max_row_nnz;
     int32_t spmv_lanes;        /* lanes per row the CSR kernel would use for this matrix */
     int64_t sell_nnz;          /* entries of the sliced-ELLPACK copy, padding included */
+    int32_t sell_dict;         /* distinct off-diagonal values of a value-indexed copy (column +
+                                  16-bit table index per entry, real diagonal apart); 0 when the
+                                  copy stores full values (complex diagonal or > 65535 values) */
+    int32_t reserved;
 } te_matrix_info;
 
 /* Synthetic model Hamiltonians built on the device (Sec. 3: the matrix of an

@@ -683,6 +683,7 @@ te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
     info->max_row_nnz = H->max_row_nnz;
     info->spmv_lanes = H->lanes;
     info->sell_nnz = H->sell_nnz;
+    info->sell_dict = H->dict_n;
     return TE_OK;
 }
 
@@ -718,6 +719,7 @@ void te_matrix_free(te_matrix* H) {
     }
     for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
                     (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_a, (void*)H->sell_pq,
+                    (void*)H->sell_idx, (void*)H->sell_diag, (void*)H->dict_a, (void*)H->dict_pq,
                     (void*)H->m3})
         if (q) cudaFree(q);
     delete H;

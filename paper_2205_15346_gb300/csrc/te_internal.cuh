@@ -101,8 +101,13 @@ struct te_matrix {
     int32_t* iperm = nullptr;    // old row -> new index
     int32_t* sell_off = nullptr; // slice offsets, nslices + 1
     int32_t* sell_col = nullptr;
-    double* sell_a = nullptr;    // Re h per stored entry
-    double2* sell_pq = nullptr;  // (Im h - Re h, Re h + Im h) per stored entry (3M product)
+    double* sell_a = nullptr;    // full-value form: Re h per stored entry
+    double2* sell_pq = nullptr;  // full-value form: (Im h - Re h, Re h + Im h) (3M product)
+    uint16_t* sell_idx = nullptr;    // value-indexed form: table index per off-diagonal entry
+    double* sell_diag = nullptr;     // value-indexed form: Re h_ii per permuted row
+    double* dict_a = nullptr;        // value table (index 0 = 0): Re h
+    double2* dict_pq = nullptr;      // value table: (Im h - Re h, Re h + Im h)
+    int32_t dict_n = 0;              // distinct off-diagonal values (0: full-value form)
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
     int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)

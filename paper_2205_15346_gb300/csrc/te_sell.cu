@@ -25,6 +25,15 @@
 // The three sums are accumulated separately over the row and combined at its
 // end.  The gathers this adds go to the load/store path, which this kernel
 // leaves mostly idle.
+//
+// Value-indexed form.  Hamiltonians built from a few couplings hold few
+// distinct off-diagonal values (tens for spin chains, thousands for bosons),
+// so the copy can store, per entry, the column and a 16-bit index into a table
+// of (a, b - a, a + b) triples, with the (real) diagonal in an array of its own:
+// 6 bytes per entry instead of 28, which leaves the product bound by FP64 issue
+// alone.  The table is found on the device with a hash set keyed on the value's
+// 128 bits; a matrix with a complex diagonal or more than 65535 distinct
+// off-diagonal values keeps the full-value form.
 #include <algorithm>
 #include <vector>
 
@@ -53,16 +62,30 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // ---------------------------------------------------------------- conversion
 
+// Stored length of each row: all entries (full-value form) or the off-diagonal
+// ones (value-indexed form, whose diagonal has an array of its own).
+__global__ void k_row_len(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          int64_t d, int offdiag, int32_t* __restrict__ len) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int b = rowptr[r], e = rowptr[r + 1];
+        int l = e - b;
+        if (offdiag)
+            for (int q = b; q < e; ++q) l -= (col[q] == r);
+        len[r] = l;
+    }
+}
+
 // One block per window: rank of each row = rows that are longer, or equally
 // long with a smaller index (a stable descending sort by length).
-__global__ void __launch_bounds__(kSigma) k_sell_rank(const int32_t* __restrict__ rowptr, int64_t d,
+__global__ void __launch_bounds__(kSigma) k_sell_rank(const int32_t* __restrict__ rowlen, int64_t d,
                                                       int32_t* __restrict__ perm,
                                                       int32_t* __restrict__ iperm) {
     __shared__ int32_t len[kSigma];
     const int64_t base = (int64_t)blockIdx.x * kSigma;
     const int n = (int)((d - base) < kSigma ? (d - base) : kSigma);
     const int t = threadIdx.x;
-    if (t < n) len[t] = rowptr[base + t + 1] - rowptr[base + t];
+    if (t < n) len[t] = rowlen[base + t];
     __syncthreads();
     if (t >= n) return;
     const int mine = len[t];
@@ -76,12 +99,179 @@ __global__ void __launch_bounds__(kSigma) k_sell_rank(const int32_t* __restrict_
 }
 
 // Entries of slice s: 32 x (length of its first, longest row).
-__global__ void k_sell_width(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
-                             int64_t d, int64_t nslices, int32_t* __restrict__ cnt) {
+__global__ void k_sell_width(const int32_t* __restrict__ rowlen, const int32_t* __restrict__ perm,
+                             int64_t nslices, int32_t* __restrict__ cnt) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= nslices) return;
-    const int64_t r = perm[s * 32];
-    cnt[s] = 32 * (rowptr[r + 1] - rowptr[r]);
+    cnt[s] = 32 * rowlen[perm[s * 32]];
+}
+
+// ---------------------------------------------------------------- value table
+
+struct alignas(16) VKey {
+    unsigned long long lo, hi;
+};
+constexpr int kDictBits = 17;
+constexpr int kDictSlots = 1 << kDictBits;     // hash slots (load factor <= 1/2)
+constexpr int kDictMax = 65535;                // distinct values (index 0 is the zero value)
+constexpr int kProbeMax = 512;
+constexpr unsigned long long kEmpty = ~0ull;   // a NaN pattern: never a stored value
+
+__device__ __forceinline__ VKey vkey(double2 v) {
+    VKey k;
+    k.lo = (unsigned long long)__double_as_longlong(v.x);
+    k.hi = (unsigned long long)__double_as_longlong(v.y);
+    return k;
+}
+
+__device__ __forceinline__ unsigned int vhash(VKey k) {
+    unsigned long long h = k.lo * 0x9E3779B97F4A7C15ull ^ (k.hi + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    return (unsigned int)(h >> (64 - kDictBits));
+}
+
+// Read of a slot that may race with its insertion; a torn read is neither empty
+// nor any finite value, so the caller treats it as "taken by another value".
+__device__ __forceinline__ VKey read_slot(const VKey* slot) {
+    const double2 raw = __ldcg(reinterpret_cast<const double2*>(slot));
+    VKey k;
+    k.lo = (unsigned long long)__double_as_longlong(raw.x);
+    k.hi = (unsigned long long)__double_as_longlong(raw.y);
+    return k;
+}
+
+// flags[0]: table full or probe limit hit; flags[1]: complex diagonal entry;
+// flags[2]: distinct values inserted.  A value may land in two slots when two
+// threads race on it (harmless: both hold the same value).
+__global__ void k_dict_insert(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double2* __restrict__ val, int64_t d, VKey* slots, int* flags) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        for (int q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+            const double2 v = val[q];
+            if (col[q] == r) {
+                if (v.y != 0.0) atomicExch(&flags[1], 1);
+                continue;
+            }
+            const VKey key = vkey(v);
+            unsigned int h = vhash(key);
+            bool placed = false;
+            for (int probe = 0; probe < kProbeMax && !placed; ++probe) {
+                VKey cur = read_slot(slots + h);
+                if (cur.lo == key.lo && cur.hi == key.hi) {
+                    placed = true;
+                } else if (cur.lo == kEmpty && cur.hi == kEmpty) {
+                    VKey empty{kEmpty, kEmpty};
+                    const VKey prev = atomicCAS(slots + h, empty, key);
+                    if (prev.lo == kEmpty && prev.hi == kEmpty) {
+                        atomicAdd(&flags[2], 1);
+                        placed = true;
+                    } else if (prev.lo == key.lo && prev.hi == key.hi) {
+                        placed = true;
+                    }
+                }
+                if (!placed) h = (h + 1) & (kDictSlots - 1);
+            }
+            if (!placed) atomicExch(&flags[0], 1);
+        }
+    }
+}
+
+// One block: dense index 1.. of every filled slot (in slot order) and the
+// table of (a, b - a, a + b); index 0 is the zero value used by padding.
+__global__ void __launch_bounds__(1024) k_dict_compact(const VKey* __restrict__ slots,
+                                                       uint16_t* __restrict__ slot_idx,
+                                                       double* __restrict__ ta,
+                                                       double2* __restrict__ tpq) {
+    __shared__ int part[1024];
+    constexpr int per = kDictSlots / 1024;
+    const int t = threadIdx.x;
+    int n = 0;
+    for (int i = 0; i < per; ++i) {
+        const VKey k = slots[t * per + i];
+        n += !(k.lo == kEmpty && k.hi == kEmpty);
+    }
+    part[t] = n;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {           // inclusive scan (Hillis-Steele)
+        const int v = (t >= o) ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int idx = 1 + part[t] - n;
+    for (int i = 0; i < per; ++i) {
+        const VKey k = slots[t * per + i];
+        if (k.lo == kEmpty && k.hi == kEmpty) continue;
+        const double a = __longlong_as_double((long long)k.lo);
+        const double b = __longlong_as_double((long long)k.hi);
+        if (idx <= kDictMax) {
+            slot_idx[t * per + i] = (uint16_t)idx;
+            ta[idx] = a;
+            tpq[idx] = make_double2(b - a, a + b);
+        }
+        ++idx;
+    }
+    if (t == 0) {
+        ta[0] = 0.0;
+        tpq[0] = make_double2(0.0, 0.0);
+    }
+}
+
+__device__ __forceinline__ uint16_t dict_find(const VKey* slots, const uint16_t* slot_idx,
+                                              double2 v, int* flags) {
+    const VKey key = vkey(v);
+    unsigned int h = vhash(key);
+    for (int probe = 0; probe < kProbeMax; ++probe) {
+        const VKey cur = slots[h];
+        if (cur.lo == key.lo && cur.hi == key.hi) return slot_idx[h];
+        h = (h + 1) & (kDictSlots - 1);
+    }
+    atomicExch(&flags[0], 1);
+    return 0;
+}
+
+// Value-indexed slices: column and table index per off-diagonal entry, the real
+// diagonal per (permuted) row.
+__global__ void k_sellv_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double2* __restrict__ val, const int32_t* __restrict__ perm,
+                             const int32_t* __restrict__ iperm, const int32_t* __restrict__ off,
+                             int64_t d, int64_t nslices, const VKey* __restrict__ slots,
+                             const uint16_t* __restrict__ slot_idx, int32_t* __restrict__ scol,
+                             uint16_t* __restrict__ sidx, double* __restrict__ diag, int* flags) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nslices * 32) return;
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int64_t o = off[s];
+    const int w = (off[s + 1] - off[s]) >> 5;
+    const int32_t self = (int32_t)(i < d ? i : 0);
+    int k = 0;
+    double dg = 0.0;
+    if (i < d) {
+        const int64_t old = perm[i];
+        for (int q = rowptr[old]; q < rowptr[old + 1]; ++q) {
+            const double2 v = val[q];
+            if (col[q] == old) {
+                dg = v.x;
+                continue;
+            }
+            if (k < w) {
+                const int64_t p = o + 32ll * k + lane;
+                scol[p] = iperm[col[q]];
+                sidx[p] = dict_find(slots, slot_idx, v, flags);
+            }
+            ++k;
+        }
+        diag[i] = dg;
+    }
+    for (; k < w; ++k) {
+        const int64_t p = o + 32ll * k + lane;
+        scol[p] = self;
+        sidx[p] = 0;
+    }
 }
 
 __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -230,6 +420,113 @@ __global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sell(
     }
 }
 
+// The same product over the value-indexed slices (see the file comment): the
+// entry's (a, b - a, a + b) come from the table, the diagonal d_r from its own
+// array and enters as d_r x_r in the row's epilogue.
+__global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sellv(
+    const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+    const uint16_t* __restrict__ vidx, const double* __restrict__ ta,
+    const double2* __restrict__ tpq, const double* __restrict__ diag,
+    const double2* __restrict__ x, const double* __restrict__ xs,
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    DevState* st, int j, int mode, double* partials) {
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    double cx = 1.0, bp = 0.0;
+    if (mode == 0) {
+        if (st->status != 0 || st->done != 0 || st->stop) return;
+        cx = st->sign * st->scale[j];
+        if (j > 0) bp = st->beta[j - 1] * st->scale[j - 1];
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (nslices + kChunk - 1) / kChunk;
+    unsigned int* next = &st->counter[6];
+    for (;;) {
+        unsigned int c = 0;
+        if (lane == 0) c = atomicAdd(next, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((int64_t)c >= nchunks) break;
+        const int64_t s1 = ((int64_t)c + 1) * kChunk < nslices ? ((int64_t)c + 1) * kChunk : nslices;
+        double acc = 0.0;
+        for (int64_t s = (int64_t)c * kChunk; s < s1; ++s) {
+            const int32_t o = __ldg(off + s);
+            const int w = (__ldg(off + s + 1) - o) >> 5;
+            const uint16_t* ip = vidx + o + lane;
+            const int32_t* cp = col + o + lane;
+            double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+            int k = 0;
+            for (; k + 2 <= w; k += 2) {
+                const int q0 = __ldcs(ip + 32 * k), q1 = __ldcs(ip + 32 * (k + 1));
+                const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+                const double a0 = __ldg(ta + q0), a1 = __ldg(ta + q1);
+                const double2 p0 = __ldg(tpq + q0), p1 = __ldg(tpq + q1);
+                const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+                const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
+                k1 = fma(a0, z0, k1);
+                k2 = fma(p0.x, x0.x, k2);
+                k3 = fma(p0.y, x0.y, k3);
+                k1 = fma(a1, z1, k1);
+                k2 = fma(p1.x, x1.x, k2);
+                k3 = fma(p1.y, x1.y, k3);
+            }
+            if (k < w) {
+                const int q0 = __ldcs(ip + 32 * k);
+                const int c0 = __ldcs(cp + 32 * k);
+                const double a0 = __ldg(ta + q0);
+                const double2 p0 = __ldg(tpq + q0);
+                const double2 x0 = __ldg(x + c0);
+                const double z0 = __ldg(xs + c0);
+                k1 = fma(a0, z0, k1);
+                k2 = fma(p0.x, x0.x, k2);
+                k3 = fma(p0.y, x0.y, k3);
+            }
+            const int64_t row = s * 32 + lane;
+            if (row < d) {
+                const double2 xr = __ldg(x + row);
+                const double dg = __ldcs(diag + row);
+                double2 out = make_double2(cx * fma(dg, xr.x, k1 - k3), cx * fma(dg, xr.y, k1 + k2));
+                if (bp != 0.0) {
+                    const double2 p = __ldcs(xprev + row);
+                    out.x = fma(-bp, p.x, out.x);
+                    out.y = fma(-bp, p.y, out.y);
+                }
+                y[row] = out;
+                acc = fma(xr.x, out.x, acc);
+                acc = fma(xr.y, out.y, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            partials[c] = acc;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    unsigned int* ctr = &st->counter[1];
+    if (threadIdx.x == 0) {
+        __threadfence();
+        am_last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < nchunks; i += blockDim.x) v += __ldcg(partials + i);
+    const double tot = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        if (mode == 0) {
+            const double a = st->scale[j] * tot;
+            st->alpha[j] = a;
+            st->as_cur = a * st->scale[j];
+            st->matvecs += 1;
+        } else {
+            st->spmv_dot = tot;
+        }
+        *ctr = 0;
+        *next = 0;
+    }
+}
+
 // dst[i] = src[map[i]]  (map = perm: old -> new order; map = iperm: back);
 // with dsum, also dsum[i] = Re dst[i] + Im dst[i] for the product's 3M form.
 __global__ void k_gather(const double2* __restrict__ src, const int32_t* __restrict__ map,
@@ -244,46 +541,131 @@ __global__ void k_gather(const double2* __restrict__ src, const int32_t* __restr
 
 }  // namespace
 
+namespace {
+
+// Try the value table: returns true (and the table in H) when the diagonal is
+// real and the off-diagonal values fit a 16-bit index.
+te_status build_dict(te_ctx* ctx, te_matrix* H, VKey** slots_out, uint16_t** slot_idx_out,
+                     int** flags_out, bool* ok) {
+    cudaStream_t s = ctx->stream;
+    *ok = false;
+    VKey* slots = nullptr;
+    uint16_t* slot_idx = nullptr;
+    int* flags = nullptr;
+    TE_CUDA_TRY(ctx, cudaMalloc(&slots, sizeof(VKey) * kDictSlots));
+    *slots_out = slots;
+    TE_CUDA_TRY(ctx, cudaMalloc(&slot_idx, sizeof(uint16_t) * kDictSlots));
+    *slot_idx_out = slot_idx;
+    TE_CUDA_TRY(ctx, cudaMalloc(&flags, sizeof(int) * 4));
+    *flags_out = flags;
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(slots, 0xff, sizeof(VKey) * kDictSlots, s));
+    TE_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * 4, s));
+    const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * 8));
+    k_dict_insert<<<grid, TE_BLOCK, 0, s>>>(H->rowptr, H->col, H->val, H->d, slots, flags);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    int hf[4] = {0, 0, 0, 0};
+    TE_CUDA_TRY(ctx, cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hf[0] || hf[1] || hf[2] > kDictMax) return TE_OK;
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->dict_a, sizeof(double) * (size_t)(hf[2] + 1)));
+    TE_CUDA_TRY(ctx, cudaMalloc(&H->dict_pq, sizeof(double2) * (size_t)(hf[2] + 1)));
+    k_dict_compact<<<1, 1024, 0, s>>>(slots, slot_idx, H->dict_a, H->dict_pq);
+    TE_CUDA_TRY(ctx, cudaGetLastError());
+    H->dict_n = hf[2];
+    *ok = true;
+    return TE_OK;
+}
+
+}  // namespace
+
 te_status build_sell(te_ctx* ctx, te_matrix* H) {
     cudaStream_t s = ctx->stream;
     const int64_t d = H->d;
     const int64_t nslices = (d + 31) / 32;
     const int64_t windows = (d + kSigma - 1) / kSigma;
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->perm, sizeof(int32_t) * (size_t)nslices * 32));
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->iperm, sizeof(int32_t) * (size_t)d));
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_off, sizeof(int32_t) * (size_t)(nslices + 1)));
-    // rows past d (in the last slice) map to row 0's length: give perm a valid entry there
-    TE_CUDA_TRY(ctx, cudaMemsetAsync(H->perm, 0, sizeof(int32_t) * (size_t)nslices * 32, s));
-    k_sell_rank<<<(int)windows, kSigma, 0, s>>>(H->rowptr, d, H->perm, H->iperm);
-    TE_CUDA_TRY(ctx, cudaGetLastError());
+    VKey* slots = nullptr;
+    uint16_t* slot_idx = nullptr;
+    int* flags = nullptr;
+    int32_t* rowlen = nullptr;
     int32_t* cnt = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&cnt, sizeof(int32_t) * (size_t)nslices));
-    k_sell_width<<<(int)((nslices + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(H->rowptr, H->perm,
-                                                                                d, nslices, cnt);
-    cudaError_t e = cudaGetLastError();
+    auto cleanup = [&]() {
+        for (void* q : {(void*)slots, (void*)slot_idx, (void*)flags, (void*)rowlen, (void*)cnt})
+            if (q) cudaFree(q);
+    };
+    bool dict = false;
+    te_status st = build_dict(ctx, H, &slots, &slot_idx, &flags, &dict);
+    if (st) {
+        cleanup();
+        return st;
+    }
+    if (!dict) {
+        if (H->dict_a) cudaFree(H->dict_a);
+        if (H->dict_pq) cudaFree(H->dict_pq);
+        H->dict_a = nullptr;
+        H->dict_pq = nullptr;
+        H->dict_n = 0;
+    }
+    cudaError_t e = cudaMalloc(&H->perm, sizeof(int32_t) * (size_t)nslices * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&H->iperm, sizeof(int32_t) * (size_t)d);
+    if (e == cudaSuccess) e = cudaMalloc(&H->sell_off, sizeof(int32_t) * (size_t)(nslices + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&rowlen, sizeof(int32_t) * (size_t)d);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(int32_t) * (size_t)nslices);
+    // rows past d (in the last slice) map to row 0's length: give perm a valid entry there
+    if (e == cudaSuccess) e = cudaMemsetAsync(H->perm, 0, sizeof(int32_t) * (size_t)nslices * 32, s);
+    const int64_t want = (d + TE_BLOCK - 1) / TE_BLOCK;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * 8));
+    if (e == cudaSuccess) {
+        k_row_len<<<grid, TE_BLOCK, 0, s>>>(H->rowptr, H->col, d, dict ? 1 : 0, rowlen);
+        k_sell_rank<<<(int)windows, kSigma, 0, s>>>(rowlen, d, H->perm, H->iperm);
+        k_sell_width<<<(int)((nslices + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(rowlen, H->perm,
+                                                                                    nslices, cnt);
+        e = cudaGetLastError();
+    }
     int64_t total = 0;
-    te_status st = TE_OK;
     if (e == cudaSuccess) st = scan_counts(ctx, cnt, nslices, H->sell_off, &total, s);
-    cudaFree(cnt);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "k_sell_width");
-    if (st) return st;
+    if (e != cudaSuccess || st) {
+        cleanup();
+        return e != cudaSuccess ? cuda_error(ctx, e, "building the sliced copy") : st;
+    }
     H->nslices = nslices;
     H->sell_nnz = total;
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_col, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1)));
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_a, sizeof(double) * (size_t)std::max<int64_t>(total, 1)));
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->sell_pq, sizeof(double2) * (size_t)std::max<int64_t>(total, 1)));
-    k_sell_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
-        H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,
-        H->sell_a, H->sell_pq);
-    TE_CUDA_TRY(ctx, cudaGetLastError());
+    const size_t tot1 = (size_t)std::max<int64_t>(total, 1);
+    e = cudaMalloc(&H->sell_col, sizeof(int32_t) * tot1);
+    if (dict) {
+        if (e == cudaSuccess) e = cudaMalloc(&H->sell_idx, sizeof(uint16_t) * tot1);
+        if (e == cudaSuccess) e = cudaMalloc(&H->sell_diag, sizeof(double) * (size_t)d);
+        if (e == cudaSuccess) {
+            k_sellv_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
+                H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, slots,
+                slot_idx, H->sell_col, H->sell_idx, H->sell_diag, flags);
+            e = cudaGetLastError();
+        }
+    } else {
+        if (e == cudaSuccess) e = cudaMalloc(&H->sell_a, sizeof(double) * tot1);
+        if (e == cudaSuccess) e = cudaMalloc(&H->sell_pq, sizeof(double2) * tot1);
+        if (e == cudaSuccess) {
+            k_sell_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
+                H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,
+                H->sell_a, H->sell_pq);
+            e = cudaGetLastError();
+        }
+    }
+    int hf[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess && dict) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "filling the sliced copy");
+    if (dict && hf[0]) return set_error(ctx, TE_ERR_INTERNAL, "value table lookup failed");
     H->sell_grid = sell_grid(nslices, ctx->num_sms);
-    TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return TE_OK;
 }
 
 int sell_grid(int64_t nslices, int num_sms) {
-    int nb = 0;
+    int nb = 0, nb2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sell, TE_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_spmv_sellv, TE_BLOCK, 0);
+    nb = std::min(nb, nb2);
     if (nb < 1) nb = 1;
     const int64_t need = (nslices + (TE_BLOCK / 32) - 1) / (TE_BLOCK / 32);
     const int64_t full = (int64_t)nb * num_sms;
@@ -295,9 +677,15 @@ int sell_grid(int64_t nslices, int num_sms) {
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,
                              double* partials, cudaStream_t s) {
-    k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_a, H->sell_pq,
-                                                 x, xs, xprev, y, H->d, H->nslices, st, j, mode,
-                                                 partials);
+    if (H->sell_idx)
+        k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_idx,
+                                                      H->dict_a, H->dict_pq, H->sell_diag, x, xs,
+                                                      xprev, y, H->d, H->nslices, st, j, mode,
+                                                      partials);
+    else
+        k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_a,
+                                                     H->sell_pq, x, xs, xprev, y, H->d, H->nslices,
+                                                     st, j, mode, partials);
     return cudaGetLastError();
 }
 

@@ -74,3 +74,59 @@ def test_spmv_single_row(te, ctx):
         assert y[0] == (2.5 - 1j) * 1j and dot == 2.5
     finally:
         te.te_matrix_free(H)
+
+
+@pytest.mark.parametrize("nvals,complex_diag,expect_table", [
+    (100, False, True),      # few distinct values, real diagonal: value-indexed copy
+    (None, False, False),    # every value distinct (> 65535): full-value copy
+    (100, True, False),      # complex diagonal: full-value copy
+])
+def test_spmv_value_table_forms(te, ctx, nvals, complex_diag, expect_table):
+    """The sliced copy stores a 16-bit index into a table of distinct
+    off-diagonal values when it can; both forms give the oracle's product."""
+    d, per = 5000, 20
+    offs = 1 + (W.uniform(201, per) * (d - 1)).astype(np.int64)
+    offs = np.unique(offs)
+    rows = np.repeat(np.arange(d), offs.size)
+    cols = (rows + np.tile(offs, d)) % d
+    n = rows.size
+    if nvals is None:
+        u = W.uniform(202, 2 * n)
+        vals = (u[:n] - 0.5) + 1j * (u[n:] - 0.5)
+    else:
+        u = W.uniform(203, 2 * nvals)
+        table = (u[:nvals] - 0.5) + 1j * (u[nvals:] - 0.5)
+        pick = (W.uniform(204, n) * nvals).astype(np.int64)
+        vals = table[pick]
+    dg = W.uniform(205, 2 * d) - 0.5
+    dvals = dg[:d] + (1j * dg[d:] if complex_diag else 0.0)
+    rows = np.concatenate([rows, np.arange(d)])
+    cols = np.concatenate([cols, np.arange(d)])
+    vals = np.concatenate([vals, dvals])
+    A = models.coo_to_csr(d, rows, cols, vals).to_scipy()
+    H = te.te_build_csr(ctx, d, rows, cols, vals)
+    try:
+        info = te.te_matrix_info_get(H)
+        if expect_table:
+            off = A.tocoo()
+            mask = off.row != off.col
+            distinct = len(np.unique(np.stack([off.data[mask].real, off.data[mask].imag], 1), axis=0))
+            assert 0 < info["sell_dict"] <= distinct + 64     # racing inserts may repeat a value
+        else:
+            assert info["sell_dict"] == 0
+        check_spmv(te, ctx, H, A, 14)
+        check_spmv(te, ctx, H, A, 15, torch_dev=True)
+    finally:
+        te.te_matrix_free(H)
+
+
+@pytest.mark.parametrize("params", [
+    W.tfim_params(10, 1), W.xxzdm_params(12, 2), W.bose_params(8, 5, 4), W.memory_params(),
+], ids=lambda p: p["model"])
+def test_model_matrices_use_value_table(te, ctx, params):
+    """The built-in models have real diagonals and few distinct couplings."""
+    H = te.te_build_model(ctx, params)
+    try:
+        assert te.te_matrix_info_get(H)["sell_dict"] > 0
+    finally:
+        te.te_matrix_free(H)
