@@ -163,7 +163,9 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
                          std::string("allocating the solver workspace: ") + cudaGetErrorString(e));
     }
     memset(p->st_host, 0, sizeof(DevState));
-    if (cudaMemsetAsync(p->st, 0, sizeof(DevState), s) != cudaSuccess) {
+    // the SpMV's group counters live in partials and must start at zero
+    if (cudaMemsetAsync(p->st, 0, sizeof(DevState), s) != cudaSuccess ||
+        cudaMemsetAsync(p->partials, 0, sizeof(double) * (size_t)max_grid, s) != cudaSuccess) {
         free_plan(p);
         return set_error(ctx, TE_ERR_CUDA, "preparing the solver workspace");
     }
@@ -744,8 +746,9 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
     ys = xs + d;
     double* xsum = reinterpret_cast<double*>(ys + d);
     double* parts = xsum + d;
-    cudaError_t e = cudaSuccess;
-    if (dev) {
+    cudaError_t e = cudaMemsetAsync(parts, 0, sizeof(double) * (size_t)sell_partials(H), s);
+    if (e != cudaSuccess) {
+    } else if (dev) {
         e = launch_gather((const double2*)x, H->perm, d, xs, xsum, ctx->num_sms, s);
     } else {
         e = cudaMemcpyAsync(ys, x, sizeof(double2) * d, cudaMemcpyHostToDevice, s);

@@ -111,6 +111,7 @@ struct te_matrix {
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
     int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)
+    int sell_tpt = 1;            // slices per SpMV task (about 1.5K stored entries)
     // 3M form for the batched product (te_block.cu), built on first use:
     // m3[k] = a, m3[nnz + k] = b - a, m3[2 nnz + k] = a + b for val[k] = a + ib
     double* m3 = nullptr;
@@ -214,7 +215,7 @@ cudaError_t step_prepare();
 
 // SELL form (te_sell.cu)
 te_status build_sell(te_ctx* ctx, te_matrix* H);
-int sell_grid(int64_t nslices, int num_sms);
+int sell_grid(int64_t nslices, int num_sms, bool indexed);
 int64_t sell_partials(const te_matrix* H);
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,

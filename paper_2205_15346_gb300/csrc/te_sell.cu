@@ -42,7 +42,17 @@
 namespace {
 
 constexpr int kSigma = 1024;     // rows per sorting window (multiple of 32)
-constexpr int kChunk = 4;        // slices per work item of the SpMV
+constexpr int kGroup = 256;      // tasks per group of the two-level Re<x, Hx> sum
+constexpr int64_t kCtrMin = 4096; // partials the other reduction kernels may use from index 0
+constexpr int kTaskEntries = 1536;   // stored entries per SpMV task (slices are grouped to this)
+
+// The SpMV keeps per-group counters in its partials buffer, above what the other
+// reduction kernels of a restart write (they use at most kCtrMin entries from 0),
+// so they persist (at zero) from one launch to the next.
+__host__ __device__ __forceinline__ int64_t sell_ctr_offset(int64_t ntasks) {
+    const int64_t ngroups = (ntasks + kGroup - 1) / kGroup;
+    return ntasks + ngroups > kCtrMin ? ntasks + ngroups : kCtrMin;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -309,21 +319,121 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
 
 // ---------------------------------------------------------------- SpMV
 
+// Slice products of the two stored forms.  row() returns, for the lane's row of
+// slice s, the sums k1 = sum a (x + y), k2 = sum (b - a) x, k3 = sum (a + b) y
+// over its stored entries, combined as (k1 - k3, k1 + k2), plus the diagonal
+// term d_r x_r of the value-indexed form.
+struct FullSlices {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ col;
+    const double* __restrict__ va;
+    const double2* __restrict__ vpq;
+    __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
+                                           const double* __restrict__ xs, int64_t r,
+                                           double2 xr) const {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const double* ap = va + o + lane;
+        const double2* qp = vpq + o + lane;
+        const int32_t* cp = col + o + lane;
+        double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 2 <= w; k += 2) {
+            const double a0 = __ldcs(ap + 32 * k), a1 = __ldcs(ap + 32 * (k + 1));
+            const double2 q0 = __ldcs(qp + 32 * k), q1 = __ldcs(qp + 32 * (k + 1));
+            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(q0.x, x0.x, k2);
+            k3 = fma(q0.y, x0.y, k3);
+            k1 = fma(a1, z1, k1);
+            k2 = fma(q1.x, x1.x, k2);
+            k3 = fma(q1.y, x1.y, k3);
+        }
+        if (k < w) {
+            const double a0 = __ldcs(ap + 32 * k);
+            const double2 q0 = __ldcs(qp + 32 * k);
+            const int c0 = __ldcs(cp + 32 * k);
+            const double2 x0 = __ldg(x + c0);
+            const double z0 = __ldg(xs + c0);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(q0.x, x0.x, k2);
+            k3 = fma(q0.y, x0.y, k3);
+        }
+        return make_double2(k1 - k3, k1 + k2);
+    }
+};
+
+struct IndexedSlices {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ col;
+    const uint16_t* __restrict__ vidx;
+    const double* __restrict__ ta;
+    const double2* __restrict__ tpq;
+    const double* __restrict__ diag;
+    __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
+                                           const double* __restrict__ xs, int64_t r,
+                                           double2 xr) const {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const uint16_t* ip = vidx + o + lane;
+        const int32_t* cp = col + o + lane;
+        double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 2 <= w; k += 2) {
+            const int q0 = __ldcs(ip + 32 * k), q1 = __ldcs(ip + 32 * (k + 1));
+            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+            const double a0 = __ldg(ta + q0), a1 = __ldg(ta + q1);
+            const double2 p0 = __ldg(tpq + q0), p1 = __ldg(tpq + q1);
+            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(p0.x, x0.x, k2);
+            k3 = fma(p0.y, x0.y, k3);
+            k1 = fma(a1, z1, k1);
+            k2 = fma(p1.x, x1.x, k2);
+            k3 = fma(p1.y, x1.y, k3);
+        }
+        if (k < w) {
+            const int q0 = __ldcs(ip + 32 * k);
+            const int c0 = __ldcs(cp + 32 * k);
+            const double a0 = __ldg(ta + q0);
+            const double2 p0 = __ldg(tpq + q0);
+            const double2 x0 = __ldg(x + c0);
+            const double z0 = __ldg(xs + c0);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(p0.x, x0.x, k2);
+            k3 = fma(p0.y, x0.y, k3);
+        }
+        const double dg = r >= 0 ? __ldcs(diag + r) : 0.0;
+        return make_double2(fma(dg, xr.x, k1 - k3), fma(dg, xr.y, k1 + k2));
+    }
+};
+
 // mode 0: Lanczos step j (y = sign scale[j] H u_j - beta[j-1] scale[j-1] u_{j-1},
 // partial Re<u_j, y>, matvec count); mode 1: y = H x and Re<x, y>.  xs[i] must
 // hold Re x_i + Im x_i.
 //
-// Work is handed out in chunks of kChunk slices through an atomic counter, so
-// SMs that run slower (far-die L2 traffic, other streams) simply take fewer
-// chunks.  Each chunk stores its own partial of Re<x, y>; the last block adds
-// the chunk partials in chunk order, so the result does not depend on which
-// warp took which chunk.
-__global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sell(
-    const int32_t* __restrict__ off, const int32_t* __restrict__ col,
-    const double* __restrict__ va, const double2* __restrict__ vpq,
-    const double2* __restrict__ x, const double* __restrict__ xs,
-    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
-    DevState* st, int j, int mode, double* partials) {
+// Each warp takes one task (tpt consecutive slices, about kTaskEntries stored
+// entries) at a time from an atomic counter, asking for the next one only when
+// it is done with the current one (reserving ahead left every warp holding an
+// unstarted task at the end and stretched the tail).  SMs that run slower simply
+// take fewer tasks, and the kernel ends within about one task of perfect
+// balance.  Re<x, y> is summed without atomics on values: every task
+// stores its warp's partial; the warp that completes a group of kGroup tasks (a
+// per-group counter tells it) adds the group's partials in task order; the last
+// CTA to finish adds the group sums in group order.  The result does not depend
+// on which warp took which task.
+template <class Slices>
+__device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* __restrict__ x,
+                                               const double* __restrict__ xs,
+                                               const double2* __restrict__ xprev,
+                                               double2* __restrict__ y, int64_t d, int64_t nslices,
+                                               int tpt, DevState* st, int j, int mode,
+                                               double* partials) {
     __shared__ double sh[32];
     __shared__ bool am_last;
     double cx = 1.0, bp = 0.0;
@@ -333,66 +443,60 @@ __global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sell(
         if (j > 0) bp = st->beta[j - 1] * st->scale[j - 1];
     }
     const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (nslices + kChunk - 1) / kChunk;
+    const int64_t ntasks = (nslices + tpt - 1) / tpt;
+    const int64_t ngroups = (ntasks + kGroup - 1) / kGroup;
+    double* gpart = partials + ntasks;
+    unsigned int* gctr = reinterpret_cast<unsigned int*>(partials + sell_ctr_offset(ntasks));
     unsigned int* next = &st->counter[6];
-    for (;;) {
-        unsigned int c = 0;
-        if (lane == 0) c = atomicAdd(next, 1u);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if ((int64_t)c >= nchunks) break;
-        const int64_t s1 = ((int64_t)c + 1) * kChunk < nslices ? ((int64_t)c + 1) * kChunk : nslices;
+    unsigned int c = 0;
+    if (lane == 0) c = atomicAdd(next, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    while ((int64_t)c < ntasks) {
+        const int64_t s0 = (int64_t)c * tpt;
+        const int64_t s1 = s0 + tpt < nslices ? s0 + tpt : nslices;
         double acc = 0.0;
-        for (int64_t s = (int64_t)c * kChunk; s < s1; ++s) {
-            const int32_t o = __ldg(off + s);
-            const int w = (__ldg(off + s + 1) - o) >> 5;
-            const double* ap = va + o + lane;
-            const double2* qp = vpq + o + lane;
-            const int32_t* cp = col + o + lane;
-            // k1 = sum a s, k2 = sum (b - a) x, k3 = sum (a + b) y
-            double k1 = 0.0, k2 = 0.0, k3 = 0.0;
-            int k = 0;
-            for (; k + 2 <= w; k += 2) {
-                const double a0 = __ldcs(ap + 32 * k), a1 = __ldcs(ap + 32 * (k + 1));
-                const double2 q0 = __ldcs(qp + 32 * k), q1 = __ldcs(qp + 32 * (k + 1));
-                const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
-                const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-                const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
-                k1 = fma(a0, z0, k1);
-                k2 = fma(q0.x, x0.x, k2);
-                k3 = fma(q0.y, x0.y, k3);
-                k1 = fma(a1, z1, k1);
-                k2 = fma(q1.x, x1.x, k2);
-                k3 = fma(q1.y, x1.y, k3);
-            }
-            if (k < w) {
-                const double a0 = __ldcs(ap + 32 * k);
-                const double2 q0 = __ldcs(qp + 32 * k);
-                const int c0 = __ldcs(cp + 32 * k);
-                const double2 x0 = __ldg(x + c0);
-                const double z0 = __ldg(xs + c0);
-                k1 = fma(a0, z0, k1);
-                k2 = fma(q0.x, x0.x, k2);
-                k3 = fma(q0.y, x0.y, k3);
-            }
+#pragma unroll 1
+        for (int64_t s = s0; s < s1; ++s) {
             const int64_t row = s * 32 + lane;
-            if (row < d) {
-                double2 out = make_double2(cx * (k1 - k3), cx * (k1 + k2));
+            const bool real_row = row < d;
+            const double2 xr = real_row ? __ldg(x + row) : make_double2(0.0, 0.0);
+            const double2 hx = M.row(s, lane, x, xs, real_row ? row : -1, xr);
+            if (real_row) {
+                double2 out = make_double2(cx * hx.x, cx * hx.y);
                 if (bp != 0.0) {
                     const double2 p = __ldcs(xprev + row);
                     out.x = fma(-bp, p.x, out.x);
                     out.y = fma(-bp, p.y, out.y);
                 }
                 y[row] = out;
-                const double2 xr = __ldg(x + row);
                 acc = fma(xr.x, out.x, acc);
                 acc = fma(xr.y, out.y, acc);
             }
         }
         acc = warp_sum(acc);
+        unsigned int done = 0;
+        const int64_t g = (int64_t)c / kGroup;
         if (lane == 0) {
             partials[c] = acc;
             __threadfence();
+            done = atomicAdd(gctr + g, 1u);
         }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        const int64_t gsize = (g + 1) * kGroup <= ntasks ? kGroup : ntasks - g * kGroup;
+        if ((int64_t)done == gsize - 1) {             // this warp finished group g
+            __threadfence();
+            double v = 0.0;
+            for (int64_t i = lane; i < gsize; i += 32) v += __ldcg(partials + g * kGroup + i);
+            v = warp_sum(v);
+            if (lane == 0) {
+                gpart[g] = v;
+                gctr[g] = 0;
+                __threadfence();
+            }
+        }
+        unsigned int cn = 0;
+        if (lane == 0) cn = atomicAdd(next, 1u);
+        c = __shfl_sync(0xffffffffu, cn, 0);
     }
     __syncthreads();
     unsigned int* ctr = &st->counter[1];
@@ -404,7 +508,7 @@ __global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sell(
     if (!am_last) return;
     __threadfence();
     double v = 0.0;
-    for (int64_t i = threadIdx.x; i < nchunks; i += blockDim.x) v += __ldcg(partials + i);
+    for (int64_t i = threadIdx.x; i < ngroups; i += blockDim.x) v += __ldcg(gpart + i);
     const double tot = block_sum(v, sh);
     if (threadIdx.x == 0) {
         if (mode == 0) {
@@ -420,111 +524,18 @@ __global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sell(
     }
 }
 
-// The same product over the value-indexed slices (see the file comment): the
-// entry's (a, b - a, a + b) come from the table, the diagonal d_r from its own
-// array and enters as d_r x_r in the row's epilogue.
-__global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sellv(
-    const int32_t* __restrict__ off, const int32_t* __restrict__ col,
-    const uint16_t* __restrict__ vidx, const double* __restrict__ ta,
-    const double2* __restrict__ tpq, const double* __restrict__ diag,
-    const double2* __restrict__ x, const double* __restrict__ xs,
+__global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sell(
+    FullSlices M, const double2* __restrict__ x, const double* __restrict__ xs,
     const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
-    DevState* st, int j, int mode, double* partials) {
-    __shared__ double sh[32];
-    __shared__ bool am_last;
-    double cx = 1.0, bp = 0.0;
-    if (mode == 0) {
-        if (st->status != 0 || st->done != 0 || st->stop) return;
-        cx = st->sign * st->scale[j];
-        if (j > 0) bp = st->beta[j - 1] * st->scale[j - 1];
-    }
-    const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (nslices + kChunk - 1) / kChunk;
-    unsigned int* next = &st->counter[6];
-    for (;;) {
-        unsigned int c = 0;
-        if (lane == 0) c = atomicAdd(next, 1u);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if ((int64_t)c >= nchunks) break;
-        const int64_t s1 = ((int64_t)c + 1) * kChunk < nslices ? ((int64_t)c + 1) * kChunk : nslices;
-        double acc = 0.0;
-        for (int64_t s = (int64_t)c * kChunk; s < s1; ++s) {
-            const int32_t o = __ldg(off + s);
-            const int w = (__ldg(off + s + 1) - o) >> 5;
-            const uint16_t* ip = vidx + o + lane;
-            const int32_t* cp = col + o + lane;
-            double k1 = 0.0, k2 = 0.0, k3 = 0.0;
-            int k = 0;
-            for (; k + 2 <= w; k += 2) {
-                const int q0 = __ldcs(ip + 32 * k), q1 = __ldcs(ip + 32 * (k + 1));
-                const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
-                const double a0 = __ldg(ta + q0), a1 = __ldg(ta + q1);
-                const double2 p0 = __ldg(tpq + q0), p1 = __ldg(tpq + q1);
-                const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-                const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
-                k1 = fma(a0, z0, k1);
-                k2 = fma(p0.x, x0.x, k2);
-                k3 = fma(p0.y, x0.y, k3);
-                k1 = fma(a1, z1, k1);
-                k2 = fma(p1.x, x1.x, k2);
-                k3 = fma(p1.y, x1.y, k3);
-            }
-            if (k < w) {
-                const int q0 = __ldcs(ip + 32 * k);
-                const int c0 = __ldcs(cp + 32 * k);
-                const double a0 = __ldg(ta + q0);
-                const double2 p0 = __ldg(tpq + q0);
-                const double2 x0 = __ldg(x + c0);
-                const double z0 = __ldg(xs + c0);
-                k1 = fma(a0, z0, k1);
-                k2 = fma(p0.x, x0.x, k2);
-                k3 = fma(p0.y, x0.y, k3);
-            }
-            const int64_t row = s * 32 + lane;
-            if (row < d) {
-                const double2 xr = __ldg(x + row);
-                const double dg = __ldcs(diag + row);
-                double2 out = make_double2(cx * fma(dg, xr.x, k1 - k3), cx * fma(dg, xr.y, k1 + k2));
-                if (bp != 0.0) {
-                    const double2 p = __ldcs(xprev + row);
-                    out.x = fma(-bp, p.x, out.x);
-                    out.y = fma(-bp, p.y, out.y);
-                }
-                y[row] = out;
-                acc = fma(xr.x, out.x, acc);
-                acc = fma(xr.y, out.y, acc);
-            }
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            partials[c] = acc;
-            __threadfence();
-        }
-    }
-    __syncthreads();
-    unsigned int* ctr = &st->counter[1];
-    if (threadIdx.x == 0) {
-        __threadfence();
-        am_last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    double v = 0.0;
-    for (int64_t i = threadIdx.x; i < nchunks; i += blockDim.x) v += __ldcg(partials + i);
-    const double tot = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        if (mode == 0) {
-            const double a = st->scale[j] * tot;
-            st->alpha[j] = a;
-            st->as_cur = a * st->scale[j];
-            st->matvecs += 1;
-        } else {
-            st->spmv_dot = tot;
-        }
-        *ctr = 0;
-        *next = 0;
-    }
+    int tpt, DevState* st, int j, int mode, double* partials) {
+    spmv_sell_body(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
+}
+
+__global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sellv(
+    IndexedSlices M, const double2* __restrict__ x, const double* __restrict__ xs,
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    int tpt, DevState* st, int j, int mode, double* partials) {
+    spmv_sell_body(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
 }
 
 // dst[i] = src[map[i]]  (map = perm: old -> new order; map = iperm: back);
@@ -630,6 +641,12 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
     }
     H->nslices = nslices;
     H->sell_nnz = total;
+    {
+        const double per_slice = (double)total / (double)nslices;
+        const double t = per_slice > 0.0 ? kTaskEntries / per_slice : 16.0;
+        // at most 4 slices: XXZ-DM L = 20 keeps only ~5 tasks per resident warp at 4
+        H->sell_tpt = (int)std::min(4.0, std::max(1.0, floor(t + 0.5)));
+    }
     const size_t tot1 = (size_t)std::max<int64_t>(total, 1);
     e = cudaMalloc(&H->sell_col, sizeof(int32_t) * tot1);
     if (dict) {
@@ -657,15 +674,14 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
     cleanup();
     if (e != cudaSuccess) return cuda_error(ctx, e, "filling the sliced copy");
     if (dict && hf[0]) return set_error(ctx, TE_ERR_INTERNAL, "value table lookup failed");
-    H->sell_grid = sell_grid(nslices, ctx->num_sms);
+    H->sell_grid = sell_grid(nslices, ctx->num_sms, dict);
     return TE_OK;
 }
 
-int sell_grid(int64_t nslices, int num_sms) {
-    int nb = 0, nb2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sell, TE_BLOCK, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_spmv_sellv, TE_BLOCK, 0);
-    nb = std::min(nb, nb2);
+int sell_grid(int64_t nslices, int num_sms, bool indexed) {
+    int nb = 0;
+    if (indexed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv, TE_BLOCK, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sell, TE_BLOCK, 0);
     if (nb < 1) nb = 1;
     const int64_t need = (nslices + (TE_BLOCK / 32) - 1) / (TE_BLOCK / 32);
     const int64_t full = (int64_t)nb * num_sms;
@@ -677,15 +693,16 @@ int sell_grid(int64_t nslices, int num_sms) {
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,
                              double* partials, cudaStream_t s) {
-    if (H->sell_idx)
-        k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_idx,
-                                                      H->dict_a, H->dict_pq, H->sell_diag, x, xs,
-                                                      xprev, y, H->d, H->nslices, st, j, mode,
-                                                      partials);
-    else
-        k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(H->sell_off, H->sell_col, H->sell_a,
-                                                     H->sell_pq, x, xs, xprev, y, H->d, H->nslices,
-                                                     st, j, mode, partials);
+    if (H->sell_idx) {
+        const IndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->dict_pq,
+                              H->sell_diag};
+        k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+                                                      H->sell_tpt, st, j, mode, partials);
+    } else {
+        const FullSlices M{H->sell_off, H->sell_col, H->sell_a, H->sell_pq};
+        k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+                                                     H->sell_tpt, st, j, mode, partials);
+    }
     return cudaGetLastError();
 }
 
@@ -697,4 +714,9 @@ cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, dou
     return cudaGetLastError();
 }
 
-int64_t sell_partials(const te_matrix* H) { return (H->nslices + kChunk - 1) / kChunk; }
+// partials the SpMV needs: per-slice and per-group sums, then the group counters
+// (which must be zero before the first launch).
+int64_t sell_partials(const te_matrix* H) {
+    const int64_t ntasks = (H->nslices + H->sell_tpt - 1) / H->sell_tpt;
+    return sell_ctr_offset(ntasks) + (ntasks + kGroup - 1) / kGroup;
+}
