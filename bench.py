@@ -192,10 +192,29 @@ def cpu_baseline_entry(wl):
                        f"solves/s = (fraction of t covered) / wall time")}
 
 
+def oracle_multi_sample(wl):
+    """The oracle's first restart of every problem of a grouped workload; the
+    group's time is estimated as the sum over problems of wall / fraction of t."""
+    from oracle import krylov, models
+    est, wall_total, matvecs = 0.0, 0.0, 0
+    for q in wl["problems"]:
+        A = models.build(q["params"]).to_scipy()
+        v0 = W.random_state(q["v0_seed"], q["d"])
+        t0 = time.perf_counter()
+        res = krylov.evolve(A, v0, q["t"], wl["tol"], wl["m"], max_restarts=1)
+        wall = time.perf_counter() - t0
+        wall_total += wall
+        matvecs += res.matvecs
+        est += wall / (abs(res.t_reached) / q["t"])
+    return len(wl["problems"]) / est, wall_total, matvecs
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if "problems" in W.workload(args.workload):
+        return run_reference_multi(args)
     wl = single_view(W.workload(args.workload))
     rates, walls = [], []
     for i in range(args.warmup + args.steps):
@@ -219,6 +238,31 @@ def run_reference(args):
     return 0
 
 
+def run_reference_multi(args):
+    wl = W.workload(args.workload)
+    rates, walls = [], []
+    for i in range(args.warmup + args.steps):
+        rate, wall, mv = oracle_multi_sample(wl)
+        if i >= args.warmup:
+            rates.append(rate)
+            walls.append(wall)
+    value = float(np.mean(rates))
+    sample = ("each step: the oracle's first restart of each of the 32 problems (1 thread); "
+              "solves/s = 32 / sum over problems of (wall / fraction of t covered)")
+    line = {
+        "metric": METRIC, "impl": "reference", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * float(np.mean(walls)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
+        "config": config_block(wl, args),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 DESCRIBE = {
     "xxzdm_L22": "XXZ-DM chain L=22 periodic, d=4194304, nnz=50331648, Neel v0",
     "xxzdm_L20": "XXZ-DM chain L=20 periodic, d=1048576, nnz=11534336, random v0",
@@ -229,6 +273,8 @@ DESCRIBE = {
                    "N0=Nc=100, d=1565904, v0 = |N0,0,1^5,0^15>"),
     "batch_xxzdm_L20_x64": ("64 random normalised initial vectors (seeds 301..364) under one "
                             "XXZ-DM chain L=20 periodic, d=1048576, nnz=11534336"),
+    "tfim_multi_x32": ("32 independent open TFIM chains, L uniform on 10..20 (total d=9182208), "
+                       "t ~ U[1,20], random v0"),
 }
 # The paper's single-thread CPU wall time for memory_K10 (353 s, i9-9900K, Sec. 5):
 # the only workload here with a published number for the same metric.
@@ -236,6 +282,10 @@ PAPER_SOLVES_PER_S = {"memory_K10": 1.0 / 353.0}
 
 
 def config_block(wl, args):
+    if "problems" in wl:
+        return {"workload": f"{wl['name']}: {DESCRIBE[wl['name']]}, m={wl['m']}, tol={wl['tol']}",
+                "global_batch": len(wl["problems"]) * args.gpus, "parallelism": f"replicas{args.gpus}",
+                "l2": "inputs larger than L2 (Krylov blocks 4.6 GB); no flush"}
     if "nvec" in wl:
         return {"workload": f"{wl['name']}: {DESCRIBE[wl['name']]}, "
                             f"t={wl['t']}, m={wl['m']}, tol={wl['tol']}",
@@ -516,6 +566,147 @@ def run_batch(args):
     return 0
 
 
+def run_multi(args):
+    """Independent problems through te_evolve_multi (one grouped launch per
+    Lanczos step), against the same problems one at a time (te_evolve) and all
+    submitted at once to the request scheduler (te_submit)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2205_15346_gb300 import te
+
+    wl = W.workload(args.workload)
+    probs, tol, m = wl["problems"], wl["tol"], wl["m"]
+    n = len(probs)
+    ctx = te.te_create(local)
+    Hs = [te.te_build_model(ctx, q["params"]) for q in probs]
+    infos = [te.te_matrix_info_get(H) for H in Hs]
+    v0 = [W.random_state(q["v0_seed"], q["d"]) for q in probs]
+    vin = [torch.from_numpy(v).cuda() for v in v0]
+    vout = [torch.empty_like(v) for v in vin]
+    ts = [q["t"] for q in probs]
+    opt = te.make_options(profile=True)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        te.te_evolve_multi(ctx, Hs, vin, ts, tol, m, opt, v_outs=vout)
+    barrier()
+    stats = []
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, sts, _, _ = te.te_evolve_multi(ctx, Hs, vin, ts, tol, m, opt, v_outs=vout)
+            stats.append(sts)
+        ev1.record(stream)
+        barrier()
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0)
+    value = n * job_throughput(args.steps, world, elapsed)
+
+    # one at a time (te_evolve), and all at once through the request scheduler
+    single = [torch.empty_like(v) for v in vin]
+    for i in range(n):
+        te.te_evolve(ctx, Hs[i], vin[i], ts[i], tol, m, v_out=single[i])
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    worst = 0.0
+    for i in range(n):
+        te.te_evolve(ctx, Hs[i], vin[i], ts[i], tol, m, v_out=single[i])
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - a
+    for i in range(n):
+        worst = max(worst, torch.linalg.vector_norm(single[i] - vout[i]).item() / tol)
+    a = time.perf_counter()
+    reqs = [te.te_submit(ctx, Hs[i], vin[i], ts[i], tol, m) for i in range(n)]
+    for i, r in enumerate(reqs):
+        s_, _ = te.te_wait(r, -1.0, single[i])
+        te.te_request_free(r)
+    sched_s = time.perf_counter() - a
+
+    # end to end with pinned host vectors (copies inside the timed region)
+    hin = [torch.from_numpy(v).pin_memory() for v in v0]
+    hout = [torch.empty_like(h).pin_memory() for h in hin]
+    opt_e2e = te.make_options()
+    te.te_evolve_multi(ctx, Hs, [h.numpy() for h in hin], ts, tol, m, opt_e2e,
+                       v_outs=[h.numpy() for h in hout])
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        te.te_evolve_multi(ctx, Hs, [h.numpy() for h in hin], ts, tol, m, opt_e2e,
+                           v_outs=[h.numpy() for h in hout])
+    barrier()
+    e2e_value = n * job_throughput(args.steps, world, max_over_ranks(time.perf_counter() - t0))
+
+    # roofline of the grouped SpMV (KM1): executed FP64 work over all its launches
+    def flops_per_matvec(info):
+        d, nnz = info["d"], info["nnz"]
+        if info["sell_dict"] > 0:
+            return 6 * (nnz - d) + 16 * d
+        return 6 * nnz + 12 * d
+    fl = [flops_per_matvec(x) for x in infos]
+    total_flops = sum(sum(st[i]["matvecs"] * fl[i] for i in range(n)) for st in stats)
+    spmv_ms = sum(st[0]["spmv_ms"] for st in stats)
+    spmv_n = sum(st[0]["spmv_launches"] for st in stats)
+    peaks, kind = measured_peaks()
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = SMS * DFMA_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    achieved_tf = total_flops / (spmv_ms / 1000.0) / 1e12
+    rounds = [max(x["restarts"] for x in st) for st in stats]
+    launches = sum(2 * n + 2 + r * (4 * m + 3) for r in rounds)
+    for H in Hs:
+        te.te_matrix_free(H)
+    te.te_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "mode": "multi", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "complex128",
+            "data": "synthetic (32 seeded TFIM parameter sets, seeded random initial vectors)",
+            "config": config_block(wl, argparse.Namespace(gpus=world, workload=args.workload)),
+            "one_at_a_time": {"solves_per_s": n / solo_s,
+                              "how": "te_evolve on each problem, one after another"},
+            "scheduler_all_at_once": {"solves_per_s": n / sched_s,
+                                      "how": "te_submit of all problems, then te_wait"},
+            "grouped_over_one_at_a_time": value / (n / solo_s),
+            "max_diff_over_tol_vs_alone": worst,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak, "traffic": None,
+                         "kernel": "k_spmv_multi (KM1: grouped SpMV of all running problems)",
+                         "avg_launch_ms": spmv_ms / spmv_n,
+                         "flops": "executed FP64 work of all grouped SpMV launches / their total time",
+                         "peak_kind": ("derived FP64 pipe peak: 152 SMs x 2 DFMA lanes x 2 FLOP x "
+                                       f"{sm_max_mhz:.0f} MHz")},
+            "solve": {"restart_rounds": rounds[0],
+                      "restarts": [x["restarts"] for x in stats[0]]},
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": 16 * sum(q["d"] for q in probs),
+                    "d2h_bytes_per_step": 16 * sum(q["d"] for q in probs)},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rate, wall, mv = oracle_multi_sample(wl)
+            line["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": (f"oracle (1 thread) first restart of each of the "
+                                               f"{n} problems ({mv} matvecs, {wall:.1f} s); solves/s = "
+                                               f"{n} / sum of (wall / fraction of t covered)")}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_serve(args):
     """Serving: a Poisson stream of mixed requests through te_submit / te_poll,
     against the same requests solved one at a time (te_evolve)."""
@@ -621,6 +812,8 @@ def main():
         return run_serve(args)
     if "nvec" in W.workload(args.workload):
         return run_batch(args)
+    if "problems" in W.workload(args.workload):
+        return run_multi(args)
     return run_ours(args)
 
 

@@ -295,6 +295,35 @@ te_status te_evolve_batch(te_ctx* ctx, const te_matrix* H, int32_t nvec, const d
                           double t, double tol, int32_t m, const te_options* opt, double* v_out,
                           te_stats* st, int32_t* status);
 
+/* Largest number of problems advanced together by te_evolve_multi; more run in
+ * consecutive groups of this size. */
+#define TE_MULTI_MAX 256
+
+/* n independent solves v_out[i] = exp(-i H[i] t[i]) v_in[i], each to within
+ * err_max = tol (Algorithm 1 for every problem; the paper solves one problem at
+ * a time and has no grouped form).  The problems may have different H (of any
+ * dimension), v and t, and keep separate Krylov spaces, steps and restart
+ * counts; what they share is the launches: each Lanczos step of all running
+ * problems is one grouped kernel launch, and the restarts run as rounds of one
+ * captured CUDA graph, so small problems do not pay a launch latency per step.
+ *   H: n matrices of this context (the same matrix may appear several times);
+ *   v_in, v_out: n complex128 vectors, v_in[i] / v_out[i] of length H[i]'s d;
+ *     device pointers if opt->flags has TE_PTR_DEVICE, else host;
+ *   t: n times (t = 0 returns v_in after checking its norm; t < 0 evolves with -H);
+ *   tol, m, opt: shared; m is clamped to each problem's d; opt->reorth must be
+ *     TE_REORTH_NONE; TE_OPT_PROFILE times the grouped SpMV launches (spmv_ms
+ *     is then the group's total, repeated in its problems);
+ *   st, status: NULL or n entries (per-problem statistics and te_status; a
+ *     failed problem does not stop the others).
+ * Returns TE_OK when every problem succeeded, else the first problem's error, or
+ * a call-level error (TE_ERR_INVALID_ARG, TE_ERR_UNSUPPORTED, TE_ERR_CUDA,
+ * TE_ERR_OOM).  Device memory: (m + 1) D 16 + D 8 bytes, D = sum of the
+ * dimensions rounded up to multiples of 32. */
+te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
+                          const double* const* v_in, const double* t, double tol, int32_t m,
+                          const te_options* opt, double* const* v_out, te_stats* st,
+                          int32_t* status);
+
 /* ---- asynchronous requests --------------------------------------------- */
 
 /* Queue a solve with the same meaning as te_evolve.  v_in is copied before the

@@ -505,6 +505,7 @@ void te_destroy(te_ctx* ctx) {
     for (Plan* p : ctx->plans) free_plan(p);
     ctx->plans.clear();
     block_plans_release(ctx, 0);
+    multi_plans_release(ctx, 0);
     if (ctx->spmv_st) cudaFree(ctx->spmv_st);
     if (ctx->spmv_st_host) cudaFreeHost(ctx->spmv_st_host);
     if (ctx->spmv_partials) cudaFree(ctx->spmv_partials);
@@ -718,6 +719,7 @@ void te_matrix_free(te_matrix* H) {
         }
         for (Plan* p : drop) free_plan(p);
         block_plans_release(ctx, H->id);
+        multi_plans_release(ctx, H->id);
     }
     for (void* q : {(void*)H->rowptr, (void*)H->col, (void*)H->val, (void*)H->perm,
                     (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_a, (void*)H->sell_pq,
@@ -818,6 +820,44 @@ te_status te_evolve_batch(te_ctx* ctx, const te_matrix* H, int32_t nvec, const d
         const size_t off = (size_t)g * 2 * (size_t)H->d;
         s = run_block_solve(ctx, H, n, v_in + off, t, tol, mu, o, v_out + off, dev,
                             st ? st + g : nullptr, status ? status + g : nullptr, ctx->stream);
+        if (s == TE_ERR_CUDA || s == TE_ERR_OOM || s == TE_ERR_INTERNAL) return s;
+        if (s != TE_OK && worst == TE_OK) {
+            worst = s;
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            first_err = ctx->err;
+        }
+    }
+    if (worst != TE_OK) set_error(ctx, worst, first_err);
+    return worst;
+}
+
+te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
+                          const double* const* v_in, const double* t, double tol, int32_t m,
+                          const te_options* opt, double* const* v_out, te_stats* st,
+                          int32_t* status) {
+    if (!ctx) return TE_ERR_INVALID_ARG;
+    if (n < 1) return set_error(ctx, TE_ERR_INVALID_ARG, "n must be >= 1");
+    if (!H || !v_in || !t || !v_out) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL array");
+    te_options o;
+    resolve_options(opt, &o);
+    for (int32_t i = 0; i < n; ++i) {
+        if (!v_in[i] || !v_out[i]) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL vector");
+        te_status s = check_solve_args(ctx, H[i], t[i], tol, m, o);
+        if (s) return s;
+        if (H[i]->ctx != ctx) return set_error(ctx, TE_ERR_INVALID_ARG, "H belongs to another context");
+    }
+    if (o.reorth != TE_REORTH_NONE)
+        return set_error(ctx, TE_ERR_UNSUPPORTED, "grouped solves use the three-term recurrence only");
+    enter(ctx);
+    if (te_status s = join_user_stream(ctx)) return s;
+    const bool dev = (o.flags & TE_PTR_DEVICE) != 0;
+    te_status worst = TE_OK;
+    std::string first_err;
+    for (int32_t g = 0; g < n; g += TE_MULTI_MAX) {
+        const int k = std::min<int32_t>(TE_MULTI_MAX, n - g);
+        te_status s = run_multi_solve(ctx, k, H + g, v_in + g, t + g, tol, m, o, v_out + g, dev,
+                                      st ? st + g : nullptr, status ? status + g : nullptr,
+                                      ctx->stream);
         if (s == TE_ERR_CUDA || s == TE_ERR_OOM || s == TE_ERR_INTERNAL) return s;
         if (s != TE_OK && worst == TE_OK) {
             worst = s;

@@ -240,6 +240,12 @@ void block_plans_release(te_ctx* ctx, uint64_t matrix_id);    // matrix_id 0: al
 te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const double* v_in, double t,
                           double tol, int m, const te_options& o, double* v_out, bool dev,
                           te_stats* stats, int32_t* status, cudaStream_t s);
+// grouped independent solves (te_multi.cu)
+void multi_plans_release(te_ctx* ctx, uint64_t matrix_id);    // matrix_id 0: all of ctx
+te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const double* const* v_in,
+                          const double* t, double tol, int m, const te_options& o,
+                          double* const* v_out, bool dev, te_stats* stats, int32_t* status,
+                          cudaStream_t s);
 // Gauss-Legendre nodes and weights on [-1, 1] (te_capi.cu)
 void gauss_legendre_table(int n, double* x, double* w);
 

@@ -1,0 +1,716 @@
+// te_multi.cu -- many independent solves (each its own H, v, t) advanced together.
+//
+// Algorithm 1 of arXiv 2205.15346 runs per problem; what a group of small and
+// large problems gains from running together is that every Lanczos step of all
+// of them is one launch instead of one per problem, so the small problems stop
+// paying a launch latency per step and fill the GPU beside the large ones.  The
+// problems keep separate Krylov spaces, states, steps and restart counts: the
+// restarts run in lock step (one CUDA graph per round), each problem's state is
+// updated only while it runs, and a finished problem drops out of the work.
+//
+// Layout: the Krylov blocks of all problems are concatenated (problem p at
+// element offset elem0_p of every block), each problem in the length-sorted
+// basis of its own sliced copy.  Work items:
+//   * SpMV tasks (tpt_p slices of problem p), numbered problem after problem and
+//     handed out by an atomic counter;
+//   * element chunks (kChunkElems consecutive elements of one problem) for the
+//     streaming kernels, assigned to CTAs by a fixed grid stride.
+// Every reduction keeps one partial per task or chunk, and one CTA per problem
+// adds the partials of its problem in order, so results do not depend on which
+// warp or CTA did which item.
+//
+// Kernels of one Lanczos step: KM1 k_spmv_multi, KM1r k_alpha_multi, KM2
+// k_orth_multi, KM2r k_decide_multi.  Per round: K3 (k_step, one CTA per
+// problem), KM4 k_recombine_multi, KM4r k_beta0_multi, state copy.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "te_internal.cuh"
+#include "te_slices.cuh"
+
+using te_slices::FullSlices;
+using te_slices::IndexedSlices;
+
+struct MProb {
+    const int32_t* off;
+    const int32_t* col;
+    const uint16_t* vidx;      // value-indexed form (null: full-value form)
+    const double* ta;
+    const double2* tpq;
+    const double* diag;
+    const double* va;          // full-value form
+    const double2* vpq;
+    int64_t d;
+    int64_t nslices;
+    int64_t elem0;             // element offset in every concatenated block
+    int32_t tpt;               // slices per SpMV task
+    int32_t pad;
+};
+
+namespace {
+
+constexpr int kChunkElems = 2048;   // elements per chunk of the streaming kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    return warp_sum(r);
+}
+
+__device__ __forceinline__ double sum_range(const double* p, int64_t n, double* sh) {
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(p + i);
+    return block_sum(v, sh);
+}
+
+// Problem of item c: the last p with start[p] <= c (start has n + 1 entries).
+__device__ __forceinline__ int owner(const int64_t* start, int n, int64_t c) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// A problem takes part in Lanczos step j while it runs and j is inside its
+// Krylov dimension (m_p = min(m, d_p)).
+__device__ __forceinline__ bool step_idle(const DevState* s, int j) {
+    return s->status != 0 || s->done != 0 || s->stop != 0 || j >= s->m;
+}
+
+// ---------------------------------------------------------------- KM1
+
+template <class Slices>
+__device__ __forceinline__ double run_task(const Slices& M, int64_t s0, int64_t s1, int lane,
+                                           int64_t d, const double2* __restrict__ x,
+                                           const double* __restrict__ xs,
+                                           const double2* __restrict__ xprev,
+                                           double2* __restrict__ y, double cx, double bp) {
+    double acc = 0.0;
+#pragma unroll 1
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t row = s * 32 + lane;
+        const bool real_row = row < d;
+        const double2 xr = real_row ? __ldg(x + row) : make_double2(0.0, 0.0);
+        const double2 hx = M.row(s, lane, x, xs, real_row ? row : -1, xr);
+        if (real_row) {
+            double2 out = make_double2(cx * hx.x, cx * hx.y);
+            if (bp != 0.0) {
+                const double2 p = __ldcs(xprev + row);
+                out.x = fma(-bp, p.x, out.x);
+                out.y = fma(-bp, p.y, out.y);
+            }
+            y[row] = out;
+            acc = fma(xr.x, out.x, acc);
+            acc = fma(xr.y, out.y, acc);
+        }
+    }
+    return acc;
+}
+
+// Lanczos step j of every running problem: y_p = s_p H_p u_p - b_p u_{p,j-1},
+// one partial of Re<u_p, y_p> per task.
+__global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_multi(
+    const MProb* __restrict__ probs, const int64_t* __restrict__ task_start, int n,
+    const double2* __restrict__ X, const double* __restrict__ S, const double2* __restrict__ Xp,
+    double2* __restrict__ Y, DevState* st, int j, double* partials, unsigned int* ctr) {
+    __shared__ int64_t ts[TE_MULTI_MAX + 1];
+    __shared__ bool am_last;
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) ts[i] = task_start[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t total = ts[n];
+    for (;;) {
+        unsigned int c = 0;
+        if (lane == 0) c = atomicAdd(&ctr[0], 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((int64_t)c >= total) break;
+        const int p = owner(ts, n, c);
+        const DevState* sp = st + p;
+        if (step_idle(sp, j)) continue;
+        const double cx = sp->sign * sp->scale[j];
+        const double bp = j > 0 ? sp->beta[j - 1] * sp->scale[j - 1] : 0.0;
+        const MProb P = probs[p];
+        const int64_t s0 = ((int64_t)c - ts[p]) * P.tpt;
+        const int64_t s1 = s0 + P.tpt < P.nslices ? s0 + P.tpt : P.nslices;
+        const double2* x = X + P.elem0;
+        const double* xs = S + P.elem0;
+        const double2* xprev = Xp ? Xp + P.elem0 : nullptr;
+        double2* y = Y + P.elem0;
+        double acc;
+        if (P.vidx) {
+            const IndexedSlices M{P.off, P.col, P.vidx, P.ta, P.tpq, P.diag};
+            acc = run_task(M, s0, s1, lane, P.d, x, xs, xprev, y, cx, bp);
+        } else {
+            const FullSlices M{P.off, P.col, P.va, P.vpq};
+            acc = run_task(M, s0, s1, lane, P.d, x, xs, xprev, y, cx, bp);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) partials[c] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        am_last = (atomicAdd(&ctr[1], 1u) == gridDim.x - 1);
+        if (am_last) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+        }
+    }
+}
+
+// KM1r: alpha_p = scale_p[j]^2 Re<u_p, y_p> (one CTA per problem).
+__global__ void __launch_bounds__(TE_BLOCK) k_alpha_multi(DevState* st, const int64_t* task_start,
+                                                          const double* partials, int j) {
+    __shared__ double sh[32];
+    DevState* sp = st + blockIdx.x;
+    if (step_idle(sp, j)) return;
+    const int64_t t0 = task_start[blockIdx.x];
+    const double tot = sum_range(partials + t0, task_start[blockIdx.x + 1] - t0, sh);
+    if (threadIdx.x == 0) {
+        const double a = sp->scale[j] * tot;
+        sp->alpha[j] = a;
+        sp->as_cur = a * sp->scale[j];
+        sp->matvecs += 1;
+    }
+}
+
+// ---------------------------------------------------------------- KM2 / KM2r
+
+// w = y - as_p u (in place, when the vector is needed), s = Re w + Im w,
+// ||w||^2 partial per chunk.
+__global__ void __launch_bounds__(TE_BLOCK) k_orth_multi(
+    const MProb* __restrict__ probs, const int64_t* __restrict__ chunk_start, int n,
+    double2* __restrict__ W, const double2* __restrict__ U, double* __restrict__ S,
+    const DevState* st, int j, double* partials) {
+    __shared__ int64_t cs[TE_MULTI_MAX + 1];
+    __shared__ double sh[32];
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) cs[i] = chunk_start[i];
+    __syncthreads();
+    const int64_t total = cs[n];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const int p = owner(cs, n, g);
+        const DevState* sp = st + p;
+        if (step_idle(sp, j)) continue;                  // uniform over the CTA
+        const double as = sp->as_cur;
+        const bool write = j + 1 < sp->m;
+        const int64_t e0 = probs[p].elem0, d = probs[p].d;
+        const int64_t b = e0 + (g - cs[p]) * kChunkElems;
+        const int64_t e = b + kChunkElems < e0 + d ? b + kChunkElems : e0 + d;
+        double acc = 0.0;
+        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+            double2 y = W[i];
+            const double2 u = __ldcs(U + i);
+            y.x = fma(-as, u.x, y.x);
+            y.y = fma(-as, u.y, y.y);
+            if (write) {
+                W[i] = y;
+                S[i] = y.x + y.y;
+            }
+            acc = fma(y.x, y.x, acc);
+            acc = fma(y.y, y.y, acc);
+        }
+        const double tot = block_sum(acc, sh);
+        if (threadIdx.x == 0) partials[g] = tot;
+    }
+}
+
+// KM2r: h_{j+1,j} of problem p, its breakdown test (Algorithm 1 step 1) and
+// scale_p[j+1].
+__global__ void __launch_bounds__(TE_BLOCK) k_decide_multi(DevState* st, const int64_t* chunk_start,
+                                                           const double* partials, int j) {
+    __shared__ double sh[32];
+    DevState* sp = st + blockIdx.x;
+    if (step_idle(sp, j)) return;
+    const int64_t c0 = chunk_start[blockIdx.x];
+    const double nrm = sqrt(sum_range(partials + c0, chunk_start[blockIdx.x + 1] - c0, sh));
+    if (threadIdx.x == 0) {
+        sp->beta[j] = nrm;
+        if (!(nrm >= sp->tol_rate)) {        // also catches NaN
+            if (!isfinite(nrm)) sp->status = TE_ERR_NONFINITE;
+            sp->stop = 1;
+            sp->m_eff = j + 1;
+            sp->breakdown = 1;
+        } else if (j + 1 < sp->m) {
+            sp->scale[j + 1] = 1.0 / nrm;
+        } else {
+            sp->m_eff = sp->m;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- KM0 / KM4 / beta0
+
+// init: ||v||^2 (and a non-finite marker) per chunk of the initial block, s = Re + Im.
+// Otherwise w_p = sum_{k < m_eff} coef_p[k] u_{p,k} into block 0 for the problems
+// whose step kernel took a step (Algorithm 1 step 3), s, ||w||^2 per chunk.
+__global__ void __launch_bounds__(TE_BLOCK) k_recombine_multi(
+    const MProb* __restrict__ probs, const int64_t* __restrict__ chunk_start, int n,
+    double2* __restrict__ V, double* __restrict__ S, int64_t blk, const DevState* st, int init,
+    double* partials) {
+    __shared__ int64_t cs[TE_MULTI_MAX + 1];
+    __shared__ double sh[32];
+    __shared__ double2 c[TE_M_MAX];
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) cs[i] = chunk_start[i];
+    __syncthreads();
+    const int64_t total = cs[n];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const int p = owner(cs, n, g);
+        const DevState* sp = st + p;
+        if (init ? sp->done != 0 : (sp->active == 0 || sp->status != 0)) continue;
+        const int nk = init ? 0 : sp->last_m_eff;
+        __syncthreads();                                // c[] of the previous chunk is consumed
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) c[k] = sp->coef[k];
+        __syncthreads();
+        const int64_t e0 = probs[p].elem0, d = probs[p].d;
+        const int64_t b = e0 + (g - cs[p]) * kChunkElems;
+        const int64_t e = b + kChunkElems < e0 + d ? b + kChunkElems : e0 + d;
+        double acc = 0.0;
+        bool finite = true;
+        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+            double re, im;
+            if (init) {
+                const double2 v = V[i];
+                re = v.x;
+                im = v.y;
+                finite &= isfinite(re) && isfinite(im);
+            } else {
+                re = 0.0;
+                im = 0.0;
+                for (int k = 0; k < nk; ++k) {
+                    const double2 a = __ldcs(V + (size_t)k * blk + i);
+                    re = fma(c[k].x, a.x, re);
+                    re = fma(-c[k].y, a.y, re);
+                    im = fma(c[k].x, a.y, im);
+                    im = fma(c[k].y, a.x, im);
+                }
+                V[i] = make_double2(re, im);
+            }
+            S[i] = re + im;
+            acc = fma(re, re, acc);
+            acc = fma(im, im, acc);
+        }
+        if (!finite) acc = __longlong_as_double(0x7ff8000000000000LL);
+        const double tot = block_sum(acc, sh);
+        if (threadIdx.x == 0) partials[g] = tot;
+    }
+}
+
+// beta0_p = ||w_p|| opens problem p's next Krylov space (init: validation of
+// v_in, Sec. 2.1 assumes ||v(0)|| = 1).
+__global__ void __launch_bounds__(TE_BLOCK) k_beta0_multi(DevState* st, const int64_t* chunk_start,
+                                                          const double* partials, int init) {
+    __shared__ double sh[32];
+    DevState* sp = st + blockIdx.x;
+    if (init ? sp->done != 0 : (sp->active == 0 || sp->status != 0)) return;
+    const int64_t c0 = chunk_start[blockIdx.x];
+    const double nrm = sqrt(sum_range(partials + c0, chunk_start[blockIdx.x + 1] - c0, sh));
+    if (threadIdx.x == 0) {
+        sp->beta0 = nrm;
+        sp->scale[0] = 1.0 / nrm;
+        sp->stop = 0;
+        sp->m_eff = sp->m;
+        sp->breakdown = 0;
+        sp->active = 0;
+        if (!isfinite(nrm)) sp->status = TE_ERR_NONFINITE;
+        else if (init && fabs(nrm - 1.0) > 1e-10) sp->status = TE_ERR_NOT_NORMALIZED;
+        if (init && sp->T == 0.0) sp->done = 1;       // t = 0: validated, nothing to evolve
+    }
+}
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ engine
+
+struct MultiPlan {
+    te_ctx* ctx = nullptr;
+    std::vector<uint64_t> ids;      // matrix of each problem
+    int m = 0, n = 0, profile = 0;
+    int64_t dsum = 0;
+    int64_t ntasks = 0, nchunks = 0;
+    int grid_spmv = 0, grid_stream = 0;
+    std::vector<int64_t> elem0;     // host copy of the element offsets
+    double2* V = nullptr;           // (m + 1) concatenated blocks of dsum elements
+    double* S = nullptr;
+    double* partials = nullptr;
+    DevState* st = nullptr;
+    DevState* st_host = nullptr;
+    DevState* st_init = nullptr;
+    MProb* probs = nullptr;
+    int64_t* task_start = nullptr;
+    int64_t* chunk_start = nullptr;
+    unsigned int* ctr = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;
+    bool in_use = false;
+};
+
+namespace {
+
+std::mutex g_multi_mu;
+std::vector<MultiPlan*> g_multi_plans;
+
+void free_multi_plan(MultiPlan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    for (void* q : {(void*)p->V, (void*)p->S, (void*)p->partials, (void*)p->st, (void*)p->probs,
+                    (void*)p->task_start, (void*)p->chunk_start, (void*)p->ctr})
+        if (q) cudaFree(q);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->st_init) cudaFreeHost(p->st_init);
+    delete p;
+}
+
+te_status capture_multi_round(te_ctx* ctx, MultiPlan* p, cudaStream_t s) {
+    const int64_t blk = p->dsum;
+    const int m = p->m, n = p->n;
+    TE_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+        const double2* X = p->V + (size_t)j * blk;
+        const double2* Xp = j > 0 ? p->V + (size_t)(j - 1) * blk : nullptr;
+        double2* Y = p->V + (size_t)(j + 1) * blk;
+        if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j], s, cudaEventRecordExternal);
+        if (e != cudaSuccess) break;
+        k_spmv_multi<<<p->grid_spmv, TE_BLOCK, 0, s>>>(p->probs, p->task_start, n, X, p->S, Xp, Y,
+                                                      p->st, j, p->partials, p->ctr);
+        if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
+        if (e != cudaSuccess) break;
+        k_alpha_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->task_start, p->partials, j);
+        k_orth_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, Y, X, p->S,
+                                                         p->st, j, p->partials);
+        k_decide_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->chunk_start, p->partials, j);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_step_batch(p->st, n, m, s);
+    if (e == cudaSuccess) {
+        k_recombine_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, p->V,
+                                                              p->S, blk, p->st, 0, p->partials);
+        k_beta0_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->chunk_start, p->partials, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState) * n, cudaMemcpyDeviceToHost, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "capturing the grouped restart graph");
+    }
+    if (e2 != cudaSuccess) return cuda_error(ctx, e2, "cudaStreamEndCapture");
+    cudaError_t e3 = cudaGraphInstantiate(&p->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return cuda_error(ctx, e3, "cudaGraphInstantiate (grouped restart)");
+    return TE_OK;
+}
+
+te_status create_multi_plan(te_ctx* ctx, int n, const te_matrix* const* H, int m, int profile,
+                            cudaStream_t s, MultiPlan** out) {
+    MultiPlan* p = new MultiPlan();
+    p->ctx = ctx;
+    p->m = m;
+    p->n = n;
+    p->profile = profile;
+    std::vector<MProb> hp(n);
+    std::vector<int64_t> ts(n + 1, 0), cs(n + 1, 0);
+    int64_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const te_matrix* A = H[i];
+        p->ids.push_back(A->id);
+        MProb& q = hp[i];
+        memset(&q, 0, sizeof(q));
+        q.off = A->sell_off;
+        q.col = A->sell_col;
+        q.vidx = A->sell_idx;
+        q.ta = A->dict_a;
+        q.tpq = A->dict_pq;
+        q.diag = A->sell_diag;
+        q.va = A->sell_a;
+        q.vpq = A->sell_pq;
+        q.d = A->d;
+        q.nslices = A->nslices;
+        q.tpt = A->sell_tpt;
+        q.elem0 = off;
+        p->elem0.push_back(off);
+        // keep every problem's segment 16-byte aligned and a whole number of slices
+        off += (A->d + 31) / 32 * 32;
+        ts[i + 1] = ts[i] + (A->nslices + A->sell_tpt - 1) / A->sell_tpt;
+        cs[i + 1] = cs[i] + (A->d + kChunkElems - 1) / kChunkElems;
+    }
+    p->dsum = off;
+    p->ntasks = ts[n];
+    p->nchunks = cs[n];
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_multi, TE_BLOCK, 0);
+    p->grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>((p->ntasks + 7) / 8,
+                                                                (int64_t)std::max(occ, 1) * ctx->num_sms));
+    p->grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>(p->nchunks, (int64_t)ctx->num_sms * 8));
+    const size_t npart = (size_t)std::max(p->ntasks, p->nchunks);
+    cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)p->dsum);
+    if (e == cudaSuccess) e = cudaMalloc(&p->S, sizeof(double) * (size_t)p->dsum);
+    if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * npart);
+    if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&p->probs, sizeof(MProb) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&p->task_start, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->chunk_start, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->ctr, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState) * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->probs, hp.data(), sizeof(MProb) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->task_start, ts.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->chunk_start, cs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ctr, 0, sizeof(unsigned int) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->st, 0, sizeof(DevState) * n, s);
+    // the gaps between segments are never written: keep them at zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->S, 0, sizeof(double) * (size_t)p->dsum, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_multi_plan(p);
+        return set_error(ctx, e == cudaErrorMemoryAllocation ? TE_ERR_OOM : TE_ERR_CUDA,
+                         std::string("allocating the grouped workspace: ") + cudaGetErrorString(e));
+    }
+    if (profile) {
+        p->ev.resize(2 * (size_t)m);
+        for (auto& ev : p->ev) cudaEventCreate(&ev);
+    }
+    te_status st = capture_multi_round(ctx, p, s);
+    if (st) {
+        free_multi_plan(p);
+        return st;
+    }
+    *out = p;
+    return TE_OK;
+}
+
+te_status acquire_multi_plan(te_ctx* ctx, int n, const te_matrix* const* H, int m, int profile,
+                             cudaStream_t s, MultiPlan** out) {
+    {
+        std::lock_guard<std::mutex> lk(g_multi_mu);
+        for (MultiPlan* p : g_multi_plans) {
+            if (p->ctx != ctx || p->in_use || p->n != n || p->m != m || p->profile != profile) continue;
+            bool same = true;
+            for (int i = 0; i < n && same; ++i) same = p->ids[i] == H[i]->id;
+            if (!same) continue;
+            p->in_use = true;
+            *out = p;
+            return TE_OK;
+        }
+    }
+    MultiPlan* p = nullptr;
+    te_status st = create_multi_plan(ctx, n, H, m, profile, s, &p);
+    if (st == TE_ERR_OOM) {
+        std::vector<MultiPlan*> idle;
+        {
+            std::lock_guard<std::mutex> lk(g_multi_mu);
+            auto it = std::partition(g_multi_plans.begin(), g_multi_plans.end(),
+                                     [&](MultiPlan* q) { return q->ctx != ctx || q->in_use; });
+            idle.assign(it, g_multi_plans.end());
+            g_multi_plans.erase(it, g_multi_plans.end());
+        }
+        cudaStreamSynchronize(s);
+        for (MultiPlan* q : idle) free_multi_plan(q);
+        st = create_multi_plan(ctx, n, H, m, profile, s, &p);
+    }
+    if (st) return st;
+    p->in_use = true;
+    std::lock_guard<std::mutex> lk(g_multi_mu);
+    g_multi_plans.push_back(p);
+    *out = p;
+    return TE_OK;
+}
+
+}  // namespace
+
+// Drop the grouped plans of a context (matrix_id 0) or those that use one matrix.
+void multi_plans_release(te_ctx* ctx, uint64_t matrix_id) {
+    std::vector<MultiPlan*> drop;
+    {
+        std::lock_guard<std::mutex> lk(g_multi_mu);
+        auto it = std::partition(g_multi_plans.begin(), g_multi_plans.end(), [&](MultiPlan* q) {
+            if (q->ctx != ctx) return true;
+            if (matrix_id == 0) return false;
+            return std::find(q->ids.begin(), q->ids.end(), matrix_id) == q->ids.end();
+        });
+        drop.assign(it, g_multi_plans.end());
+        g_multi_plans.erase(it, g_multi_plans.end());
+    }
+    for (MultiPlan* p : drop) free_multi_plan(p);
+}
+
+// One group of n <= TE_MULTI_MAX problems.
+te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const double* const* v_in,
+                          const double* t, double tol, int m, const te_options& o,
+                          double* const* v_out, bool dev, te_stats* stats, int32_t* status,
+                          cudaStream_t s) {
+    const double t0 = now_ms();
+    const int profile = (o.flags & TE_OPT_PROFILE) ? 1 : 0;
+    MultiPlan* p = nullptr;
+    te_status rs = acquire_multi_plan(ctx, n, H, m, profile, s, &p);
+    if (rs) return rs;
+    auto release = [&]() {
+        std::lock_guard<std::mutex> lk(g_multi_mu);
+        p->in_use = false;
+    };
+    auto fail = [&](cudaError_t e, const char* what) {
+        release();
+        return cuda_error(ctx, e, what);
+    };
+    DevState* ini = p->st_init;
+    memset(ini, 0, sizeof(DevState) * n);
+    double gx[TE_GAUSS_MAX], gw[TE_GAUSS_MAX];
+    gauss_legendre_table(o.gauss_n, gx, gw);
+    for (int i = 0; i < n; ++i) {
+        DevState& x = ini[i];
+        const double ti = t[i];
+        x.T = fabs(ti);
+        x.tol_rate = (ti != 0.0) ? tol / fabs(ti) : tol;
+        x.sign = (ti >= 0.0) ? 1.0 : -1.0;
+        x.t_step0 = o.t_step0;
+        x.shrink = o.shrink;
+        x.quad_rel_tol = o.quad_rel_tol;
+        x.min_step = o.min_step_rel * fabs(ti);
+        x.m = (int)std::min<int64_t>(m, H[i]->d);
+        x.n_substeps = o.n_substeps;
+        x.quad = o.quad;
+        x.gauss_n = o.gauss_n;
+        x.quad_max_levels = o.quad_max_levels;
+        x.max_substeps = o.max_substeps;
+        x.smallexp = o.small_exp;
+        x.first = 1;
+        x.m_eff = x.m;
+        x.min_err_step = INFINITY;
+        memcpy(x.gx, gx, sizeof(gx));
+        memcpy(x.gw, gw, sizeof(gw));
+    }
+    const int64_t blk = p->dsum;
+    double2* stage = p->V + (size_t)m * (size_t)blk;   // the last block is free outside a round
+    cudaError_t e = cudaMemcpyAsync(p->st, ini, sizeof(DevState) * n, cudaMemcpyHostToDevice, s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const int64_t d = H[i]->d;
+        double2* seg = p->V + p->elem0[i];
+        const double2* src = (const double2*)v_in[i];
+        if (!dev) {
+            e = cudaMemcpyAsync(stage + p->elem0[i], v_in[i], sizeof(double2) * d,
+                                cudaMemcpyHostToDevice, s);
+            src = stage + p->elem0[i];
+        }
+        if (e == cudaSuccess)
+            e = launch_gather(src, H[i]->perm, d, seg, p->S + p->elem0[i], ctx->num_sms, s);
+    }
+    if (e == cudaSuccess) {
+        k_recombine_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, p->V,
+                                                              p->S, blk, p->st, 1, p->partials);
+        k_beta0_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->chunk_start, p->partials, 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e, "starting the grouped solve");
+    const DevState* h = p->st_host;
+    double spmv_ms = 0.0;
+    int64_t spmv_launches = 0, rounds = 0;
+    auto running = [&]() {
+        for (int i = 0; i < n; ++i)
+            if (h[i].status == 0 && h[i].done == 0 && t[i] != 0.0) return true;
+        return false;
+    };
+    while (running()) {
+        e = cudaGraphLaunch(p->exec, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(e, "grouped restart round");
+        ++rounds;
+        if (profile) {
+            for (int j = 0; j < m; ++j) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, p->ev[2 * j], p->ev[2 * j + 1]) == cudaSuccess) {
+                    spmv_ms += ms;
+                    spmv_launches += 1;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const int64_t d = H[i]->d;
+        const double2* seg = p->V + p->elem0[i];
+        if (dev) {
+            e = launch_gather(seg, H[i]->iperm, d, (double2*)v_out[i], nullptr, ctx->num_sms, s);
+        } else {
+            e = launch_gather(seg, H[i]->iperm, d, stage + p->elem0[i], nullptr, ctx->num_sms, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(v_out[i], stage + p->elem0[i], sizeof(double2) * d,
+                                    cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e, "returning the grouped results");
+    te_status worst = TE_OK;
+    const double el = now_ms() - t0;
+    for (int i = 0; i < n; ++i) {
+        const DevState& x = h[i];
+        const te_status si = x.status;
+        if (status) status[i] = si;
+        if (si != TE_OK && worst == TE_OK) worst = si;
+        if (!stats) continue;
+        const double per_restart = (double)H[i]->d * H[i]->norm1 * 2.220446049250313e-16;
+        te_stats S;
+        memset(&S, 0, sizeof(S));
+        S.norm_in = x.beta0;
+        S.m_used = x.m;
+        S.restarts = x.restarts;
+        S.matvecs = x.matvecs;
+        S.breakdowns = x.breakdowns;
+        S.quad_warnings = x.quad_warnings;
+        S.quad_integrals = x.quad_integrals;
+        S.quad_nodes = x.quad_nodes;
+        S.eig_mcycles = 1e-6 * (double)x.eig_cycles;
+        S.search_mcycles = 1e-6 * (double)x.search_cycles;
+        S.err_bound = x.err_acc;
+        S.roundoff_est = per_restart * (double)x.restarts;
+        if (x.restarts > 0 && per_restart > x.min_err_step) S.flags |= TE_WARN_ROUNDOFF;
+        if (x.breakdowns) S.flags |= TE_FLAG_BREAKDOWN;
+        if (x.quad_warnings) S.flags |= TE_WARN_QUAD;
+        S.t_reached = (t[i] == 0.0) ? 0.0 : (t[i] >= 0.0 ? 1.0 : -1.0) * x.t_now;
+        S.spmv_ms = spmv_ms;
+        S.spmv_launches = spmv_launches;
+        S.solve_ms = el;
+        stats[i] = S;
+    }
+    if (worst == TE_ERR_NOT_NORMALIZED)
+        set_error(ctx, worst, "an input vector is not normalised (| ||v|| - 1 | > 1e-10)");
+    else if (worst == TE_ERR_NONFINITE)
+        set_error(ctx, worst, "non-finite values in a grouped solve");
+    else if (worst == TE_ERR_STEP_UNDERFLOW)
+        set_error(ctx, worst, "step size underflow in a grouped solve");
+    else if (worst != TE_OK)
+        set_error(ctx, worst, "grouped solve failed on the device");
+    release();
+    (void)rounds;
+    return worst;
+}

@@ -1,0 +1,105 @@
+// te_slices.cuh -- row products of the two sliced-ELLPACK forms of H, shared by
+// the single-solve SpMV (te_sell.cu) and the grouped SpMV of many independent
+// problems (te_multi.cu).  See te_sell.cu for the storage and the
+// three-multiplication product.
+#pragma once
+
+#include "te_internal.cuh"
+
+namespace te_slices {
+
+// Slice products of the two stored forms.  row() returns, for the lane's row of
+// slice s, the sums k1 = sum a (x + y), k2 = sum (b - a) x, k3 = sum (a + b) y
+// over its stored entries, combined as (k1 - k3, k1 + k2), plus the diagonal
+// term d_r x_r of the value-indexed form.
+struct FullSlices {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ col;
+    const double* __restrict__ va;
+    const double2* __restrict__ vpq;
+    __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
+                                           const double* __restrict__ xs, int64_t r,
+                                           double2 xr) const {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const double* ap = va + o + lane;
+        const double2* qp = vpq + o + lane;
+        const int32_t* cp = col + o + lane;
+        double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 2 <= w; k += 2) {
+            const double a0 = __ldcs(ap + 32 * k), a1 = __ldcs(ap + 32 * (k + 1));
+            const double2 q0 = __ldcs(qp + 32 * k), q1 = __ldcs(qp + 32 * (k + 1));
+            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(q0.x, x0.x, k2);
+            k3 = fma(q0.y, x0.y, k3);
+            k1 = fma(a1, z1, k1);
+            k2 = fma(q1.x, x1.x, k2);
+            k3 = fma(q1.y, x1.y, k3);
+        }
+        if (k < w) {
+            const double a0 = __ldcs(ap + 32 * k);
+            const double2 q0 = __ldcs(qp + 32 * k);
+            const int c0 = __ldcs(cp + 32 * k);
+            const double2 x0 = __ldg(x + c0);
+            const double z0 = __ldg(xs + c0);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(q0.x, x0.x, k2);
+            k3 = fma(q0.y, x0.y, k3);
+        }
+        return make_double2(k1 - k3, k1 + k2);
+    }
+};
+
+struct IndexedSlices {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ col;
+    const uint16_t* __restrict__ vidx;
+    const double* __restrict__ ta;
+    const double2* __restrict__ tpq;
+    const double* __restrict__ diag;
+    __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
+                                           const double* __restrict__ xs, int64_t r,
+                                           double2 xr) const {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const uint16_t* ip = vidx + o + lane;
+        const int32_t* cp = col + o + lane;
+        double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 2 <= w; k += 2) {
+            const int q0 = __ldcs(ip + 32 * k), q1 = __ldcs(ip + 32 * (k + 1));
+            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+            const double a0 = __ldg(ta + q0), a1 = __ldg(ta + q1);
+            const double2 p0 = __ldg(tpq + q0), p1 = __ldg(tpq + q1);
+            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(p0.x, x0.x, k2);
+            k3 = fma(p0.y, x0.y, k3);
+            k1 = fma(a1, z1, k1);
+            k2 = fma(p1.x, x1.x, k2);
+            k3 = fma(p1.y, x1.y, k3);
+        }
+        if (k < w) {
+            const int q0 = __ldcs(ip + 32 * k);
+            const int c0 = __ldcs(cp + 32 * k);
+            const double a0 = __ldg(ta + q0);
+            const double2 p0 = __ldg(tpq + q0);
+            const double2 x0 = __ldg(x + c0);
+            const double z0 = __ldg(xs + c0);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(p0.x, x0.x, k2);
+            k3 = fma(p0.y, x0.y, k3);
+        }
+        const double dg = r >= 0 ? __ldcs(diag + r) : 0.0;
+        return make_double2(fma(dg, xr.x, k1 - k3), fma(dg, xr.y, k1 + k2));
+    }
+};
+
+}  // namespace te_slices

@@ -105,6 +105,8 @@ _SIGS = {
                               C.POINTER(te_options), _P, C.POINTER(te_stats)]),
     "te_evolve_batch": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_double, C.c_double, C.c_int32,
                                     C.POINTER(te_options), _P, _P, _P]),
+    "te_evolve_multi": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.c_double, C.c_int32,
+                                    C.POINTER(te_options), _P, _P, _P]),
     "te_submit": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
                               C.POINTER(te_options), C.POINTER(_P)]),
     "te_poll": (C.c_int32, [_P, _P, C.POINTER(te_stats)]),
@@ -410,6 +412,43 @@ def te_evolve_batch(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options 
                               C.cast(sts, C.c_void_p), C.cast(stat, C.c_void_p))
     _check(ctx, s, allow)
     return v_out, [x.as_dict() for x in sts], [int(x) for x in stat], s
+
+
+def te_evolve_multi(ctx, Hs, v_ins, ts, tol: float, m: int, opt: te_options | None = None,
+                    v_outs=None, allow=(TE_OK,)):
+    """Independent solves exp(-i H_i t_i) v_i advanced together; returns
+    (list of outputs, list of stats dicts, list of per-problem statuses, call status)."""
+    n = len(Hs)
+    if len(v_ins) != n or len(ts) != n:
+        raise ValueError("Hs, v_ins and ts must have the same length")
+    ds = [te_matrix_info_get(H)["d"] for H in Hs]
+    ins = [_vec_ptr(v, d) for v, d in zip(v_ins, ds)]
+    dev = ins[0][1]
+    if any(x[1] != dev for x in ins):
+        raise ValueError("all vectors must be host arrays or all device tensors")
+    if v_outs is None:
+        if dev:
+            import torch
+            v_outs = [torch.empty_like(v) for v in v_ins]
+        else:
+            v_outs = [np.empty(d, dtype=np.complex128) for d in ds]
+    outs = [_vec_ptr(v, d, writable=True) for v, d in zip(v_outs, ds)]
+    if any(x[1] != dev for x in outs):
+        raise ValueError("outputs must live where the inputs do")
+    o = te_options.from_buffer_copy(opt if opt is not None else te_default_options())
+    o.flags = (o.flags & ~TE_PTR_DEVICE) | (TE_PTR_DEVICE if dev else 0)
+    Harr = (C.c_void_p * n)(*[C.c_void_p(H.value if isinstance(H, C.c_void_p) else H) for H in Hs])
+    inarr = (C.c_void_p * n)(*[x[0] for x in ins])
+    outarr = (C.c_void_p * n)(*[x[0] for x in outs])
+    tarr = (C.c_double * n)(*[float(x) for x in ts])
+    sts = (te_stats * n)()
+    stat = (C.c_int32 * n)()
+    s = lib().te_evolve_multi(ctx, n, C.cast(Harr, C.c_void_p), C.cast(inarr, C.c_void_p),
+                              C.cast(tarr, C.c_void_p), float(tol), int(m), C.byref(o),
+                              C.cast(outarr, C.c_void_p), C.cast(sts, C.c_void_p),
+                              C.cast(stat, C.c_void_p))
+    _check(ctx, s, allow)
+    return v_outs, [x.as_dict() for x in sts], [int(x) for x in stat], s
 
 
 def te_submit(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None):

@@ -152,6 +152,15 @@ def workload(name: str) -> dict:
         p = xxzdm_params(20, seed=3)
         return {"name": name, "params": p, "d": 1 << 20, "nvec": 64,
                 "v0_seeds": list(range(301, 365)), "t": 50.0, "m": 40, "tol": 1e-8}
+    if name == "tfim_multi_x32":
+        # 32 independent open TFIM chains: L uniform on 10..20, t ~ U[1, 20]
+        u = uniform(6, 64)
+        probs = []
+        for i in range(32):
+            L = 10 + min(int(u[2 * i] * 11), 10)
+            probs.append({"params": tfim_params(L, seed=800 + i), "d": 1 << L,
+                          "t": float(1.0 + 19.0 * u[2 * i + 1]), "v0_seed": 900 + i})
+        return {"name": name, "problems": probs, "m": 30, "tol": 1e-8}
     if name == "memory_K10":
         p = memory_params(K=10, Kp=10, N0=100, Nm=5, Nc=100.0)
         return {"name": name, "params": p, "d": memory_dim(p),
