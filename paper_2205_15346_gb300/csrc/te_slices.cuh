@@ -70,11 +70,20 @@ struct IndexedSlices {
         const uint16_t* ip = vidx + o + lane;
         const int32_t* cp = col + o + lane;
         double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        // columns and table indices are loaded one pair ahead of their gathers
+        int c0 = 0, c1 = 0, q0 = 0, q1 = 0;
+        if (w >= 2) {
+            c0 = __ldcs(cp); c1 = __ldcs(cp + 32);
+            q0 = __ldcs(ip); q1 = __ldcs(ip + 32);
+        }
         int k = 0;
 #pragma unroll 1
         for (; k + 2 <= w; k += 2) {
-            const int q0 = __ldcs(ip + 32 * k), q1 = __ldcs(ip + 32 * (k + 1));
-            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
+            int n0 = 0, n1 = 0, m0 = 0, m1 = 0;
+            if (k + 4 <= w) {
+                n0 = __ldcs(cp + 32 * (k + 2)); n1 = __ldcs(cp + 32 * (k + 3));
+                m0 = __ldcs(ip + 32 * (k + 2)); m1 = __ldcs(ip + 32 * (k + 3));
+            }
             const double a0 = __ldg(ta + q0), a1 = __ldg(ta + q1);
             const double2 p0 = __ldg(tpq + q0), p1 = __ldg(tpq + q1);
             const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
@@ -85,14 +94,15 @@ struct IndexedSlices {
             k1 = fma(a1, z1, k1);
             k2 = fma(p1.x, x1.x, k2);
             k3 = fma(p1.y, x1.y, k3);
+            c0 = n0; c1 = n1; q0 = m0; q1 = m1;
         }
         if (k < w) {
-            const int q0 = __ldcs(ip + 32 * k);
-            const int c0 = __ldcs(cp + 32 * k);
-            const double a0 = __ldg(ta + q0);
-            const double2 p0 = __ldg(tpq + q0);
-            const double2 x0 = __ldg(x + c0);
-            const double z0 = __ldg(xs + c0);
+            const int qq = __ldcs(ip + 32 * k);
+            const int cc = __ldcs(cp + 32 * k);
+            const double a0 = __ldg(ta + qq);
+            const double2 p0 = __ldg(tpq + qq);
+            const double2 x0 = __ldg(x + cc);
+            const double z0 = __ldg(xs + cc);
             k1 = fma(a0, z0, k1);
             k2 = fma(p0.x, x0.x, k2);
             k3 = fma(p0.y, x0.y, k3);
