@@ -38,7 +38,8 @@ import workloads as W  # noqa: E402
 METRIC = "exp(-iHt)v solves/s and p50/p99 latency at bound 1e-8; SpMV HBM GB/s vs peak"
 WORKLOAD = "xxzdm_L22"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_spmv_sellv_xxzdm_L22.md")
-K1_SOURCE = os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", "te_sell.cu")
+K1_SOURCES = [os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", f)
+              for f in ("te_sell.cu", "te_slices.cuh")]
 # FP64 issue rate of GB300: 2 DFMA lanes per SM per cycle (ncu reports a sustained
 # peak of 304 DFMA thread-instructions per cycle over the 152 SMs)
 SMS = 152
@@ -79,8 +80,12 @@ def measured_peaks():
 
 
 def k1_source_hash() -> str:
-    with open(K1_SOURCE, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the K1 sources (te_sell.cu + te_slices.cuh)."""
+    h = hashlib.sha256()
+    for f in K1_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic():
