@@ -383,3 +383,27 @@ def memory_norm1(p: dict, basis: MemoryBasis | None = None) -> float:
             bos += abs(p["C0"] * math.sqrt(m0) * math.sqrt(n0 + 1))
         best = max(best, float(np.max(diag + hop + bos)))
     return best
+
+
+# ---------------------------------------------------------------- observables
+
+def occupation(p: dict, l: int) -> np.ndarray:
+    """Number operator of mode l as the diagonal over the model's basis (float64).
+
+    Spin chains: mode l is site l and n_l = 1 when spin l points down (bit l of
+    the index).  Bosons: the occupation of mode l.  The paper's example system
+    (Sec. 5): mode 0 is a_0 (n0), mode 1 is b_0 (m0), modes 2.. are the qubits
+    a_1..a_K, a'_1..a'_K' -- the number operators whose expectation values the
+    paper plots over time.
+    """
+    kind = p["model"]
+    if kind in ("tfim", "xxzdm"):
+        d = 1 << p["L"]
+        return ((np.arange(d, dtype=np.int64) >> l) & 1).astype(np.float64)
+    if kind == "bose":
+        b = BoseBasis(p["K"], p["N"])
+        return np.array([s[l] for s in b.states], dtype=np.float64)
+    if kind == "memory":
+        b = MemoryBasis(p)
+        return np.array([b.state(r)[l] for r in range(len(b))], dtype=np.float64)
+    raise KeyError(kind)
