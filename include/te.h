@@ -268,6 +268,42 @@ te_status te_spmv_noalloc(te_ctx* ctx, const te_matrix* H, const double* x, doub
 te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
                     int32_t m, const te_options* opt, double* v_out, te_stats* st);
 
+/* v_out = exp(-i H t) v_in as te_evolve, plus the states at intermediate times
+ * (the extension remarked in Sec. 2.4: inside a step, the restart's H_m and V_m
+ * give the state at any time the step covers, so sampling costs no extra
+ * restarts) and diagonal observables of those states.
+ *   t_samples: n_samples >= 1 host doubles with the sign of t (or 0), |s| <= |t|,
+ *     non-decreasing |s|.  A sample is evaluated in the first restart whose step
+ *     reaches it.
+ *   v_samples: NULL or n_samples complex128 vectors of length d one after another
+ *     (device if opt->flags has TE_PTR_DEVICE, else host).
+ *   obs: NULL or n_obs real diagonal observables of length d one after another
+ *     (O_l[i] = <i|O_l|i>, same pointer kind as v_in); obs_out: host,
+ *     n_samples x n_obs doubles, obs_out[s n_obs + l] = sum_i O_l[i] |v_s[i]|^2.
+ *   sample_bounds: NULL or n_samples host doubles: the error bound accumulated
+ *     through the step that produced each sample (eq. errorIntegral; it also
+ *     covers the sample, whose integral is a part of the step's).
+ *   v_out must not be NULL; opt->spmv_lanes must be 0.
+ * Device memory: that of te_evolve plus n_samples d 16 bytes (the samples) and,
+ * with observables, n_obs d 8 bytes.  Errors as te_evolve; samples the solve did
+ * not reach are left at zero. */
+te_status te_evolve_sampled(te_ctx* ctx, const te_matrix* H, const double* v_in, double t,
+                            int32_t n_samples, const double* t_samples, double tol, int32_t m,
+                            const te_options* opt, double* v_out, double* v_samples, int32_t n_obs,
+                            const double* obs, double* obs_out, double* sample_bounds,
+                            te_stats* st);
+
+/* Number operator of one mode as a diagonal over the model's basis:
+ * out[i] = <i| n_mode |i> for every basis index i (out: d doubles, device if
+ * flags has TE_PTR_DEVICE, else host).  Spin chains: mode l is site l, n_l = 1
+ * when spin l points down (bit l of the index).  Bosons: occupation of mode l.
+ * The paper's example system (Sec. 5): mode 0 = a_0, mode 1 = b_0, modes 2.. =
+ * the qubits a_1..a_K, a'_1..a'_K' -- the observables whose expectation values
+ * the paper plots over time.  Errors: TE_ERR_INVALID_ARG (unknown model, mode
+ * out of range), TE_ERR_CUDA, TE_ERR_OOM. */
+te_status te_model_occupation(te_ctx* ctx, const te_model_desc* desc, int32_t mode, double* out,
+                              uint32_t flags);
+
 /* Largest number of vectors in one block product of te_evolve_batch; larger
  * batches run in consecutive groups of this size. */
 #define TE_BATCH_MAX 64

@@ -747,3 +747,91 @@ int64_t memory_rank_host(const te_model_desc* m, const int32_t* occ) {
     if (ones != T.Nm) return -1;
     return (long long)(T.N0 - n0) * T.nq + mem_rank(T, mask);
 }
+
+// ---------------------------------------------------------------- occupations
+
+namespace {
+
+__global__ void k_occ_spin(int64_t d, int l, double* __restrict__ out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[r] = (double)((r >> l) & 1);
+}
+
+__global__ void k_occ_bose(BoseTables T, int64_t d, int l, double* __restrict__ out) {
+    int occ[16];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        bose_unrank(T, r, occ);
+        out[r] = (double)occ[l];
+    }
+}
+
+__global__ void k_occ_memory(MemTables T, int64_t d, int l, double* __restrict__ out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const long long b = r / T.nq;
+        double v;
+        if (l == 0) v = (double)(T.N0 - b);
+        else if (l == 1) v = (double)b;
+        else v = (double)((mem_unrank(T, r - b * T.nq) >> (l - 2)) & 1u);
+        out[r] = v;
+    }
+}
+
+}  // namespace
+
+extern "C" te_status te_model_occupation(te_ctx* ctx, const te_model_desc* desc, int32_t mode,
+                                         double* out, uint32_t flags) {
+    if (!ctx || !desc || !out) return TE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaGetLastError();
+    cudaStream_t s = ctx->stream;
+    int64_t d = 0;
+    int modes = 0;
+    BoseTables BT;
+    MemTables MT;
+    switch (desc->model) {
+        case TE_MODEL_TFIM:
+        case TE_MODEL_XXZDM:
+            if (desc->L < 2 || desc->L > 30) return set_error(ctx, TE_ERR_INVALID_ARG, "L outside 2..30");
+            d = 1ll << desc->L;
+            modes = desc->L;
+            break;
+        case TE_MODEL_BOSE:
+            if (desc->L < 2 || desc->L > 16 || desc->N < 1 || desc->N > 15)
+                return set_error(ctx, TE_ERR_INVALID_ARG, "bosons need 2 <= K <= 16, 1 <= N <= 15");
+            bose_tables(desc->L, desc->N, &BT);
+            d = (int64_t)BT.comp[desc->N][desc->L];
+            modes = desc->L;
+            break;
+        case TE_MODEL_MEMORY:
+            if (desc->L < 1 || desc->L2 < 1 || desc->L + desc->L2 > 30 || desc->N < 0 ||
+                desc->N > desc->L + desc->L2 || desc->N2 < 0)
+                return set_error(ctx, TE_ERR_INVALID_ARG, "invalid memory model sizes");
+            mem_tables(desc, &MT);
+            d = (int64_t)(desc->N2 + 1) * MT.nq;
+            modes = 2 + desc->L + desc->L2;
+            break;
+        default:
+            return set_error(ctx, TE_ERR_INVALID_ARG, "unknown model");
+    }
+    if (mode < 0 || mode >= modes) return set_error(ctx, TE_ERR_INVALID_ARG, "mode outside the model");
+    const bool dev = (flags & TE_PTR_DEVICE) != 0;
+    double* dst = out;
+    if (!dev) TE_CUDA_TRY(ctx, cudaMalloc(&dst, sizeof(double) * (size_t)d));
+    const int grid = grid_for(d);
+    switch (desc->model) {
+        case TE_MODEL_TFIM:
+        case TE_MODEL_XXZDM: k_occ_spin<<<grid, TE_BLOCK, 0, s>>>(d, mode, dst); break;
+        case TE_MODEL_BOSE: k_occ_bose<<<grid, TE_BLOCK, 0, s>>>(BT, d, mode, dst); break;
+        default: k_occ_memory<<<grid, TE_BLOCK, 0, s>>>(MT, d, mode, dst); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dev)
+        e = cudaMemcpyAsync(out, dst, sizeof(double) * (size_t)d, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (!dev) cudaFree(dst);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "te_model_occupation");
+    return TE_OK;
+}

@@ -71,6 +71,8 @@ void free_plan(Plan* p) {
     if (p->partials_r) cudaFree(p->partials_r);
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->st_init) cudaFreeHost(p->st_init);
+    for (void* q : {(void*)p->samp_ts, (void*)p->samp_coef, (void*)p->samp_buf, (void*)p->samp_bound})
+        if (q) cudaFree(q);
     delete p;
 }
 
@@ -115,6 +117,9 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         }
     }
     if (e == cudaSuccess) e = launch_step(p->st, m, s);
+    if (e == cudaSuccess && p->ns > 0)
+        e = launch_sample_kernels(p->st, p->samp_ts, p->ns, m, p->samp_coef, p->samp_bound, p->V,
+                                  d, p->samp_buf, p->grid_stream, s);
     if (e == cudaSuccess)
         e = launch_recombine(p->V, p->S, d, p->st, p->partials, p->grid_stream, s);
     if (e == cudaSuccess)
@@ -132,9 +137,10 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
 }
 
 te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
-                      cudaStream_t s, Plan** out) {
+                      cudaStream_t s, Plan** out, int ns = 0) {
     Plan* p = new Plan();
     p->H = H;
+    p->ns = ns;
     p->matrix_id = H->id;
     p->m = m;
     p->reorth = reorth;
@@ -156,6 +162,12 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
         e = cudaMalloc(&p->partials_r, sizeof(double) * (size_t)p->grid_reorth * TE_M_MAX * 2);
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState));
+    if (e == cudaSuccess && ns > 0) {
+        e = cudaMalloc(&p->samp_ts, sizeof(double) * (size_t)ns);
+        if (e == cudaSuccess) e = cudaMalloc(&p->samp_coef, sizeof(double2) * (size_t)ns * m);
+        if (e == cudaSuccess) e = cudaMalloc(&p->samp_buf, sizeof(double2) * (size_t)ns * H->d);
+        if (e == cudaSuccess) e = cudaMalloc(&p->samp_bound, sizeof(double) * (size_t)ns);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
@@ -480,7 +492,8 @@ te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
         return TE_ERR_OOM;
     }
     cudaMemset(c->spmv_st, 0, sizeof(DevState));
-    if (step_prepare() != cudaSuccess || block_prepare() != cudaSuccess) {
+    if (step_prepare() != cudaSuccess || block_prepare() != cudaSuccess ||
+        sample_prepare() != cudaSuccess) {
         te_destroy(c);
         return TE_ERR_CUDA;
     }
@@ -795,6 +808,105 @@ te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
                   st, nullptr);
     release_plan(ctx, p);
     return s;
+}
+
+te_status te_evolve_sampled(te_ctx* ctx, const te_matrix* H, const double* v_in, double t,
+                            int32_t n_samples, const double* t_samples, double tol, int32_t m,
+                            const te_options* opt, double* v_out, double* v_samples, int32_t n_obs,
+                            const double* obs, double* obs_out, double* sample_bounds,
+                            te_stats* st) {
+    if (!ctx) return TE_ERR_INVALID_ARG;
+    if (!v_in || !v_out) return set_error(ctx, TE_ERR_INVALID_ARG, "NULL vector");
+    if (n_samples < 1 || !t_samples) return set_error(ctx, TE_ERR_INVALID_ARG, "need n_samples >= 1 times");
+    if (n_obs < 0 || (n_obs > 0 && (!obs || !obs_out)))
+        return set_error(ctx, TE_ERR_INVALID_ARG, "observables need obs and obs_out");
+    te_options o;
+    resolve_options(opt, &o);
+    te_status rs = check_solve_args(ctx, H, t, tol, m, o);
+    if (rs) return rs;
+    if (o.spmv_lanes != 0)
+        return set_error(ctx, TE_ERR_UNSUPPORTED, "sampled solves use the sliced SpMV (spmv_lanes 0)");
+    std::vector<double> ts(n_samples);
+    double prev = 0.0;
+    for (int32_t k = 0; k < n_samples; ++k) {
+        const double x = t_samples[k];
+        if (!isfinite(x) || (x != 0.0 && (x > 0.0) != (t > 0.0)) || fabs(x) > fabs(t) || fabs(x) < prev)
+            return set_error(ctx, TE_ERR_INVALID_ARG,
+                             "sample times must have the sign of t, |s| <= |t|, non-decreasing |s|");
+        ts[k] = fabs(x);
+        prev = ts[k];
+    }
+    enter(ctx);
+    if ((rs = join_user_stream(ctx))) return rs;
+    cudaStream_t s = ctx->stream;
+    const int64_t d = H->d;
+    const int mu = (int)std::min<int64_t>(m, d);
+    const bool dev = (o.flags & TE_PTR_DEVICE) != 0;
+    Plan* p = nullptr;
+    rs = create_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, 0, s, &p, n_samples);
+    if (rs) return rs;
+    auto done = [&](te_status r) {
+        cudaStreamSynchronize(s);
+        free_plan(p);
+        return r;
+    };
+    cudaError_t e = cudaMemcpyAsync(p->samp_ts, ts.data(), sizeof(double) * n_samples,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p->samp_buf, 0, sizeof(double2) * (size_t)n_samples * d, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->samp_bound, 0, sizeof(double) * n_samples, s);
+    if (e != cudaSuccess) return done(cuda_error(ctx, e, "preparing the sampled solve"));
+    const te_status solve = run_solve(ctx, H, p, s, v_in, t, tol, o, v_out, dev, st, nullptr);
+    if (solve == TE_ERR_CUDA || solve == TE_ERR_OOM) return done(solve);
+    // t = 0: every sample is v_in (V's first column holds it in the permuted basis)
+    if (t == 0.0 && solve == TE_OK)
+        for (int32_t k = 0; k < n_samples && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(p->samp_buf + (size_t)k * d, p->V, sizeof(double2) * d,
+                                cudaMemcpyDeviceToDevice, s);
+    double2* stage = p->V + (size_t)mu * d;           // free after the solve
+    if (v_samples) {
+        for (int32_t k = 0; k < n_samples && e == cudaSuccess; ++k) {
+            double2* dst = dev ? reinterpret_cast<double2*>(v_samples) + (size_t)k * d : stage;
+            e = launch_gather(p->samp_buf + (size_t)k * d, H->iperm, d, dst, nullptr, ctx->num_sms, s);
+            if (e == cudaSuccess && !dev)
+                e = cudaMemcpyAsync(v_samples + (size_t)k * 2 * d, stage, sizeof(double2) * d,
+                                    cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e == cudaSuccess && n_obs > 0) {
+        const int G = ctx->num_sms;
+        double *Op = nullptr, *part = nullptr, *res = nullptr;
+        e = cudaMalloc(&Op, sizeof(double) * ((size_t)n_obs * d + (size_t)n_samples * n_obs * G +
+                                              (size_t)n_samples * n_obs));
+        if (e == cudaSuccess) {
+            part = Op + (size_t)n_obs * d;
+            res = part + (size_t)n_samples * n_obs * G;
+            double* raw = reinterpret_cast<double*>(stage);   // one observable at a time
+            for (int32_t l = 0; l < n_obs && e == cudaSuccess; ++l) {
+                const double* src = obs + (size_t)l * d;
+                if (!dev) {
+                    e = cudaMemcpyAsync(raw, src, sizeof(double) * d, cudaMemcpyHostToDevice, s);
+                    src = raw;
+                }
+                if (e == cudaSuccess)
+                    e = launch_gather_real(src, H->perm, d, Op + (size_t)l * d, ctx->num_sms, s);
+                if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(s);   // raw is reused
+            }
+            if (e == cudaSuccess)
+                e = launch_observables(p->samp_buf, d, n_samples, Op, n_obs, part, G, res, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(obs_out, res, sizeof(double) * (size_t)n_samples * n_obs,
+                                    cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(Op);
+        }
+    }
+    if (e == cudaSuccess && sample_bounds)
+        e = cudaMemcpyAsync(sample_bounds, p->samp_bound, sizeof(double) * n_samples,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(cuda_error(ctx, e, "returning the samples"));
+    return done(solve);
 }
 
 te_status te_evolve_batch(te_ctx* ctx, const te_matrix* H, int32_t nvec, const double* v_in,

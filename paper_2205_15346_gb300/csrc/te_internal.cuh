@@ -75,6 +75,10 @@ struct DevState {
     double last_step;
     double last_err;
     double min_err_step;     // smallest accepted step error (roundoff comparison)
+    double win_t0, win_t1;   // |t| at the start and end of the last step taken
+    int32_t win_last;        // that step reached |t|
+    int32_t samp_next;       // first intermediate sample not yet evaluated
+    int32_t samp_lo, samp_hi;    // samples of the current window
     double scale[TE_M_MAX + 1];   // v_j = scale[j] * u_j (stored vectors are unnormalised)
     double alpha[TE_M_MAX];       // diagonal of H_m
     double beta[TE_M_MAX];        // beta[j] = h_{j+2,j+1} (0-based j); h = beta[m_eff-1]
@@ -120,6 +124,12 @@ struct te_matrix {
 // One solve's device workspace and captured restart graph.
 struct Plan {
     const te_matrix* H = nullptr;
+    // intermediate-time sampling (te_sample.cu); such plans are built per call
+    int ns = 0;                      // sample times
+    double* samp_ts = nullptr;       // device: |t_s|, non-decreasing
+    double2* samp_coef = nullptr;    // device: ns x m coefficients
+    double2* samp_buf = nullptr;     // device: ns x d sampled states (permuted basis)
+    double* samp_bound = nullptr;    // device: ns bounds
     uint64_t matrix_id = 0;
     int m = 0;
     int reorth = 0;
@@ -240,6 +250,17 @@ void block_plans_release(te_ctx* ctx, uint64_t matrix_id);    // matrix_id 0: al
 te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const double* v_in, double t,
                           double tol, int m, const te_options& o, double* v_out, bool dev,
                           te_stats* stats, int32_t* status, cudaStream_t s);
+// intermediate-time sampling (te_sample.cu)
+int sample_omega_smem(int mcap);
+cudaError_t sample_prepare();
+cudaError_t launch_sample_kernels(DevState* st, const double* ts, int ns, int mcap, double2* coef,
+                                  double* bound, const double2* V, int64_t d, double2* out,
+                                  int grid_stream, cudaStream_t s);
+cudaError_t launch_gather_real(const double* src, const int32_t* map, int64_t d, double* dst,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_observables(const double2* W, int64_t d, int ns, const double* O, int nobs,
+                               double* partials, int G, double* out, cudaStream_t s);
+
 // grouped independent solves (te_multi.cu)
 void multi_plans_release(te_ctx* ctx, uint64_t matrix_id);    // matrix_id 0: all of ctx
 te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const double* const* v_in,

@@ -36,15 +36,13 @@
 #include <float.h>
 
 #include "te_internal.cuh"
+#include "te_smallexp.cuh"
 
 namespace {
 
 constexpr double kUMax = 3.15;
 constexpr int kMinLevel = 3;
 constexpr double kHalfPi = 1.5707963267948966;
-constexpr int kKcap = 3072;          // largest Chebyshev / Bessel index
-constexpr int kMillerExtra = 20;     // backward recurrence starts this far above the last term
-constexpr double kBig = 1e250, kSmall = 1e-250;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -97,10 +95,6 @@ __device__ void block_minmax_all(double lo, double hi, double* red, double* out_
     __syncthreads();
 }
 
-// Number of Bessel terms kept at argument z: J_k(z) is below 1e-30 past it.
-__device__ __forceinline__ int bessel_terms(double z) {
-    return (int)ceil(z + 10.0 * cbrt(z) + 30.0);
-}
 
 struct Small {                       // what the integrand needs, in shared memory
     int method;                      // TE_SMALLEXP_*
@@ -570,80 +564,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
             L.om[r] = make_double2(re, im);
         }
     } else {
-        const double z = F.a * tau;
-        const int K = min(bessel_terms(fmin(z, (double)kKcap)), kKcap - kMillerExtra - 1);
-        const int M = K + kMillerExtra;
-        if (tid == 0) {
-            // J_0..J_K(z) by Miller's backward recurrence, normalised by J_0 + 2 sum J_2k
-            double* J = L.jk;
-            if (!(z > 1e-300)) {
-                J[0] = 1.0;
-                for (int k = 1; k <= K; ++k) J[k] = 0.0;
-                sh_S = 1.0;
-            } else {
-                const double inv = 2.0 / z;
-                double t = inv * M, jp = 0.0, jc = 1e-300, S = 0.0;
-                for (int k = M; k >= 0; --k) {
-                    if (k <= K) J[k] = jc;
-                    if ((k & 1) == 0) S += (k == 0) ? jc : 2.0 * jc;
-                    if (k == 0) break;
-                    const double jn = fma(t, jc, -jp);
-                    jp = jc;
-                    jc = jn;
-                    t -= inv;
-                    if (fabs(jc) > kBig) {
-                        jc *= kSmall;
-                        jp *= kSmall;
-                        S *= kSmall;
-                        for (int q = k; q <= K; ++q) J[q] *= kSmall;
-                    }
-                }
-                sh_S = S;
-            }
-        }
-        __syncthreads();
-        const double invS = 1.0 / sh_S;
-        // sum_k c_k (-i)^k J_k T_k(T~) e_1, recomputing the Chebyshev vectors
-        double* v0 = L.v3;
-        double* v1 = L.v3 + mcap;
-        double* v2 = L.v3 + 2 * mcap;
-        double accr = 0.0, acci = 0.0;
-        for (int i = tid; i < n; i += nt) {
-            v0[i] = (i == 0) ? 1.0 : 0.0;
-            v2[i] = 0.0;
-        }
-        __syncthreads();
-        double* vc = v0;
-        double* vp = v2;
-        double* vn = v1;
-        for (int k = 0; k <= K; ++k) {
-            const double c = (k == 0 ? 1.0 : 2.0) * L.jk[k] * invS;
-            if (tid < n) {
-                const double x = vc[tid];
-                switch (k & 3) {
-                    case 0: accr = fma(c, x, accr); break;
-                    case 1: acci = fma(-c, x, acci); break;
-                    case 2: accr = fma(-c, x, accr); break;
-                    default: acci = fma(c, x, acci); break;
-                }
-            }
-            if (k == K) break;
-            for (int i = tid; i < n; i += nt) {
-                double tv = (L.al[i] - F.b) * vc[i];
-                if (i > 0) tv = fma(L.be[i - 1], vc[i - 1], tv);
-                if (i + 1 < n) tv = fma(L.be[i], vc[i + 1], tv);
-                tv *= F.inv_a;
-                vn[i] = (k == 0) ? tv : 2.0 * tv - vp[i];
-            }
-            __syncthreads();
-            double* tmp = vp;
-            vp = vc;
-            vc = vn;
-            vn = tmp;
-        }
-        double sb, cb;
-        sincos(F.b * tau, &sb, &cb);                // e^{-i b tau}
-        if (tid < n) L.om[tid] = make_double2(cb * accr + sb * acci, cb * acci - sb * accr);
+        cheb_exp_e1(L.al, L.be, n, F.a, F.b, F.inv_a, tau, L.jk, L.v3, mcap, &sh_S, L.om);
     }
     __syncthreads();
     for (int r = tid; r < n; r += nt) {
@@ -656,6 +577,9 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
         st->eig_cycles += clk1 - clk0;
         st->search_cycles += clock64() - clk1;
         st->t_now = (tau == t_rem) ? T : t_now + tau;
+        st->win_t0 = t_now;                     // window of this step, for intermediate samples
+        st->win_t1 = t_now + tau;
+        st->win_last = (tau == t_rem) ? 1 : 0;
         st->err_acc += err;
         st->prev_step = tau;
         st->first = 0;

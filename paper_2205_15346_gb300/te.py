@@ -103,6 +103,10 @@ _SIGS = {
     "te_spmv_noalloc": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
                               C.POINTER(te_options), _P, C.POINTER(te_stats)]),
+    "te_evolve_sampled": (C.c_int32, [_P, _P, _P, C.c_double, C.c_int32, _P, C.c_double,
+                                      C.c_int32, C.POINTER(te_options), _P, _P, C.c_int32, _P,
+                                      _P, _P, C.POINTER(te_stats)]),
+    "te_model_occupation": (C.c_int32, [_P, C.POINTER(te_model_desc), C.c_int32, _P, C.c_uint32]),
     "te_evolve_batch": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_double, C.c_double, C.c_int32,
                                     C.POINTER(te_options), _P, _P, _P]),
     "te_evolve_multi": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.c_double, C.c_int32,
@@ -449,6 +453,79 @@ def te_evolve_multi(ctx, Hs, v_ins, ts, tol: float, m: int, opt: te_options | No
                               C.cast(stat, C.c_void_p))
     _check(ctx, s, allow)
     return v_outs, [x.as_dict() for x in sts], [int(x) for x in stat], s
+
+
+def te_model_occupation(ctx, params: dict, mode: int, out=None):
+    """Number operator of one mode over the model's basis (numpy array, or fills a
+    CUDA float64 tensor given as out)."""
+    desc, keep = model_desc(params)
+    if out is None:
+        info_d = None
+        # the dimension follows from the model; build it from the parameters
+        if params["model"] in ("tfim", "xxzdm"):
+            info_d = 1 << params["L"]
+        elif params["model"] == "bose":
+            import math
+            info_d = math.comb(params["N"] + params["K"] - 1, params["N"])
+        else:
+            import math
+            info_d = (params["N0"] + 1) * math.comb(params["K"] + params["Kp"], params["Nm"])
+        out = np.empty(info_d, dtype=np.float64)
+    if _is_torch(out):
+        ptr, flags = C.c_void_p(out.data_ptr()), TE_PTR_DEVICE if out.is_cuda else 0
+    else:
+        ptr, flags = C.c_void_p(out.ctypes.data), 0
+    _check(ctx, lib().te_model_occupation(ctx, C.byref(desc), int(mode), ptr, flags))
+    return out
+
+
+def te_evolve_sampled(ctx, H, v_in, t: float, t_samples, tol: float, m: int,
+                      opt: te_options | None = None, observables=None, want_vectors: bool = True,
+                      allow=(TE_OK,)):
+    """exp(-iHt) v_in plus the states (and diagonal observables) at t_samples.
+
+    observables: None or an (n_obs, d) float64 array (host) / CUDA tensor.
+    Returns (v_out, samples or None, obs_out (n_samples, n_obs) or None,
+    sample_bounds, stats dict, status)."""
+    d = te_matrix_info_get(H)["d"]
+    ip, idev, ik = _vec_ptr(v_in, d)
+    ts = np.ascontiguousarray(t_samples, dtype=np.float64)
+    ns = ts.size
+    if idev:
+        import torch
+        v_out = torch.empty_like(v_in)
+        samples = torch.zeros((ns, d), dtype=torch.complex128, device=v_in.device) if want_vectors else None
+    else:
+        v_out = np.empty(d, dtype=np.complex128)
+        samples = np.zeros((ns, d), dtype=np.complex128) if want_vectors else None
+    op = C.c_void_p(v_out.data_ptr() if idev else v_out.ctypes.data)
+    sp = C.c_void_p(0)
+    if samples is not None:
+        sp = C.c_void_p(samples.data_ptr() if idev else samples.ctypes.data)
+    nobs = 0
+    obp = C.c_void_p(0)
+    obs_out = None
+    okeep = None
+    if observables is not None:
+        if idev:
+            okeep = observables.contiguous()
+            nobs = okeep.shape[0]
+            obp = C.c_void_p(okeep.data_ptr())
+        else:
+            okeep = np.ascontiguousarray(observables, dtype=np.float64)
+            nobs = okeep.shape[0]
+            obp = C.c_void_p(okeep.ctypes.data)
+        obs_out = np.zeros((ns, nobs), dtype=np.float64)
+    bounds = np.zeros(ns, dtype=np.float64)
+    o = te_options.from_buffer_copy(opt if opt is not None else te_default_options())
+    o.flags = (o.flags & ~TE_PTR_DEVICE) | (TE_PTR_DEVICE if idev else 0)
+    st = te_stats()
+    s = lib().te_evolve_sampled(ctx, H, ip, float(t), ns, C.c_void_p(ts.ctypes.data), float(tol),
+                                int(m), C.byref(o), op, sp, nobs, obp,
+                                C.c_void_p(obs_out.ctypes.data) if obs_out is not None else C.c_void_p(0),
+                                C.c_void_p(bounds.ctypes.data), C.byref(st))
+    _check(ctx, s, allow)
+    return v_out, samples, obs_out, bounds, st.as_dict(), s
 
 
 def te_submit(ctx, H, v_in, t: float, tol: float, m: int, opt: te_options | None = None):
