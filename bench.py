@@ -278,6 +278,8 @@ DESCRIBE = {
                    "N0=Nc=100, d=1565904, v0 = |N0,0,1^5,0^15>"),
     "batch_xxzdm_L20_x64": ("64 random normalised initial vectors (seeds 301..364) under one "
                             "XXZ-DM chain L=20 periodic, d=1048576, nnz=11534336"),
+    "memory_K10_sampled": ("the paper's example system at its benchmark size (d=1565904) with "
+                           "all 22 mode occupations sampled at 100 times (Sec. 2.4, Sec. 5)"),
     "tfim_multi_x32": ("32 independent open TFIM chains, L uniform on 10..20 (total d=9182208), "
                        "t ~ U[1,20], random v0"),
 }
@@ -712,6 +714,99 @@ def run_multi(args):
     return 0
 
 
+def run_sampled(args):
+    """A solve with intermediate samples and observables (te_evolve_sampled),
+    against the same solve without them (te_evolve)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2205_15346_gb300 import te
+
+    wl = W.workload(args.workload)
+    p, d, t, tol, m = wl["params"], wl["d"], wl["t"], wl["tol"], wl["m"]
+    ts = wl["samples"]
+    ctx = te.te_create(local)
+    H = te.te_build_model(ctx, p)
+    L = 2 + p["K"] + p["Kp"]
+    occ = torch.stack([te.te_model_occupation(ctx, p, l, out=torch.empty(d, dtype=torch.float64,
+                                                                         device="cuda"))
+                       for l in range(L)])
+    v0 = W.initial_vector(wl["v0"], d, index_of=lambda o: te.te_model_basis_index(p, o))
+    vin = torch.from_numpy(v0).cuda()
+    opt = te.make_options()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        te.te_evolve_sampled(ctx, H, vin, t, ts, tol, m, opt, observables=occ, want_vectors=False)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, _, n, bounds, st, _ = te.te_evolve_sampled(ctx, H, vin, t, ts, tol, m, opt,
+                                                          observables=occ, want_vectors=False)
+        ev1.record(stream)
+        barrier()
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0)
+    value = job_throughput(args.steps, world, elapsed)
+    # the same solve without samples
+    vout = torch.empty_like(vin)
+    te.te_evolve(ctx, H, vin, t, tol, m, opt, v_out=vout)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    for _ in range(args.steps):
+        te.te_evolve(ctx, H, vin, t, tol, m, opt, v_out=vout)
+    torch.cuda.synchronize()
+    plain = args.steps / (time.perf_counter() - a)
+    # end to end with host buffers: v_in, v_out and the observables cross the link
+    hin = v0.copy()
+    occ_h = occ.cpu().numpy()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        te.te_evolve_sampled(ctx, H, hin, t, ts, tol, m, opt, observables=occ_h, want_vectors=False)
+    barrier()
+    e2e_value = job_throughput(args.steps, world, max_over_ranks(time.perf_counter() - t0))
+    conserved = max(float(np.max(np.abs(n[:, 0] + n[:, 1] - p["N0"]))),
+                    float(np.max(np.abs(n[:, 2:].sum(1) - p["Nm"]))))
+    launches = 4 + st["restarts"] * (2 * m + 5) + 2
+    te.te_matrix_free(H)
+    te.te_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "mode": "sampled", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": (value / PAPER_SOLVES_PER_S["memory_K10"]),
+            "dtype": "complex128", "data": "the paper's example system (deterministic parameters, Sec. 5)",
+            "config": config_block(wl, argparse.Namespace(gpus=world, workload=args.workload)),
+            "samples": len(ts), "observables": L,
+            "without_samples": {"solves_per_s": plain, "how": "te_evolve, same solve"},
+            "sampling_overhead": plain / value - 1.0,
+            "max_conservation_violation": conserved,
+            "max_sample_bound": float(np.max(bounds)),
+            "solve": {"restarts": st["restarts"], "matvecs": st["matvecs"], "err_bound": st["err_bound"]},
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": 16 * d + 8 * d * L,
+                    "d2h_bytes_per_step": 16 * d + 8 * len(ts) * L},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_serve(args):
     """Serving: a Poisson stream of mixed requests through te_submit / te_poll,
     against the same requests solved one at a time (te_evolve)."""
@@ -819,6 +914,8 @@ def main():
         return run_batch(args)
     if "problems" in W.workload(args.workload):
         return run_multi(args)
+    if "samples" in W.workload(args.workload):
+        return run_sampled(args)
     return run_ours(args)
 
 

@@ -161,6 +161,12 @@ def workload(name: str) -> dict:
             probs.append({"params": tfim_params(L, seed=800 + i), "d": 1 << L,
                           "t": float(1.0 + 19.0 * u[2 * i + 1]), "v0_seed": 900 + i})
         return {"name": name, "problems": probs, "m": 30, "tol": 1e-8}
+    if name == "memory_K10_sampled":
+        # the same solve with every mode occupation at 100 evenly spaced times
+        w = workload("memory_K10")
+        w["name"] = name
+        w["samples"] = [float(x) for x in np.linspace(0.0, w["t"], 100)]
+        return w
     if name == "memory_K10":
         p = memory_params(K=10, Kp=10, N0=100, Nm=5, Nc=100.0)
         return {"name": name, "params": p, "d": memory_dim(p),
