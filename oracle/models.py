@@ -407,3 +407,84 @@ def occupation(p: dict, l: int) -> np.ndarray:
         b = MemoryBasis(p)
         return np.array([b.state(r)[l] for r in range(len(b))], dtype=np.float64)
     raise KeyError(kind)
+
+
+# ---------------------------------------------------------------- operator expressions (Sec. 3)
+
+def operator_basis(L: int, N: int, caps=None) -> list:
+    """All occupation tuples (n_1..n_L) with sum N and n_l <= caps[l] (Sec. 3,
+    eq. totalOccupationNumber and the fixed maximal occupations of Sec. 4), in
+    descending lexicographic order; ind(state) = position in this list."""
+    caps = [N] * L if caps is None else [min(int(c), N) for c in caps]
+    out, cur = [], [0] * L
+
+    def rec(pos: int, rem: int):
+        if pos == L:
+            if rem == 0:
+                out.append(tuple(cur))
+            return
+        for a in range(min(rem, caps[pos]), -1, -1):
+            cur[pos] = a
+            rec(pos + 1, rem - a)
+        cur[pos] = 0
+
+    rec(0, N)
+    return out
+
+
+def apply_term(state: tuple, factors, caps, N: int):
+    """Apply one product of ladder operators (listed left to right; the rightmost
+    acts first) to a number state: returns (target state, product of the integer
+    factors under the square root) or None when the result is zero or leaves
+    the space.  a_l |n_l> = sqrt(n_l) |n_l - 1>, a_l^dag |n_l> = sqrt(n_l + 1) |n_l + 1>."""
+    occ = list(state)
+    prod = 1
+    for mode, dag in reversed(factors):
+        if dag:
+            occ[mode] += 1
+            if occ[mode] > caps[mode]:
+                return None
+            prod *= occ[mode]
+        else:
+            if occ[mode] == 0:
+                return None
+            prod *= occ[mode]
+            occ[mode] -= 1
+    if sum(occ) != N:
+        return None
+    return tuple(occ), prod
+
+
+def operator_csr(op: dict) -> CSR:
+    """createMatrix (Sec. 3) for a Hermitian operator given as terms.
+
+    op = {"L", "N", "caps" (or None), "terms": [(coef complex, [(mode, dagger), ...]), ...]}.
+    Row j holds <j|H|i> for the states i reached from state j: applying the
+    operator to |j> gives sum_k c_k |i_k>, i.e. <i_k|H|j> = c_k, and for a
+    Hermitian operator <j|H|i_k> = conj(c_k).  Contributions to the same column
+    are added in term order; every diagonal entry is stored.
+    """
+    L, N = op["L"], op["N"]
+    caps = [N] * L if op.get("caps") is None else [min(int(c), N) for c in op["caps"]]
+    states = operator_basis(L, N, caps)
+    index = {s: i for i, s in enumerate(states)}
+    rows, cols, vals = [], [], []
+    for j, s in enumerate(states):
+        acc = {j: 0j}
+        for coef, factors in op["terms"]:
+            r = apply_term(s, factors, caps, N)
+            if r is None:
+                continue
+            tgt, prod = r
+            i = index[tgt]
+            v = complex(coef).conjugate() * np.sqrt(float(prod))
+            acc[i] = acc.get(i, 0j) + v
+        for i in sorted(acc):
+            rows.append(j)
+            cols.append(i)
+            vals.append(acc[i])
+    d = len(states)
+    rowptr = np.zeros(d + 1, dtype=np.int64)
+    np.add.at(rowptr, np.asarray(rows, dtype=np.int64) + 1, 1)
+    return CSR(d, np.cumsum(rowptr), np.asarray(cols, dtype=np.int64),
+               np.asarray(vals, dtype=np.complex128))
