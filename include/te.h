@@ -268,6 +268,44 @@ te_status te_spmv_noalloc(te_ctx* ctx, const te_matrix* H, const double* x, doub
 te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
                     int32_t m, const te_options* opt, double* v_out, te_stats* st);
 
+/* ---- operator expressions (Sec. 3) ---------------------------------------- */
+
+/* A Hermitian operator written in creation / annihilation operators of L modes
+ * (Sec. 3), on the basis of all occupation tuples (n_1..n_L) with sum N
+ * (eq. totalOccupationNumber) and n_l <= max_occ[l] (the fixed maximal
+ * occupations of Sec. 4; max_occ = NULL: no cap), ordered descending
+ * lexicographically.  The operator is sum_t coef_t * O_{t,1} ... O_{t,k_t} with
+ * each O a_l (annihilation) or a_l^dagger (creation), applied right to left:
+ * a_l |n> = sqrt(n_l) |n - 1_l>, a_l^dagger |n> = sqrt(n_l + 1) |n + 1_l>; a
+ * result outside the basis (a cap exceeded, the total changed) contributes
+ * nothing.  The caller must pass the terms of a Hermitian operator (each
+ * non-Hermitian term together with its adjoint). */
+typedef struct te_operator_desc {
+    int32_t n_modes;            /* L, 1..32 */
+    int32_t n_particles;        /* N, 0..64 */
+    const int32_t* max_occ;     /* NULL or L maximal occupations */
+    int32_t n_terms;            /* 0..4096 */
+    const int32_t* term_len;    /* n_terms: ladder operators in each term, 0..8 (0: coef * identity) */
+    const int32_t* modes;       /* sum of term_len: the mode of each operator, left to right */
+    const int32_t* dagger;      /* sum of term_len: 1 creation, 0 annihilation */
+    const double* coef;         /* 2 n_terms: (re, im) of each term's coefficient */
+} te_operator_desc;
+
+/* createMatrix (Sec. 3) on the device: H[j][i] = <j|H|i>, built row by row from
+ * the terms applied to basis state j; contributions to one entry are added in
+ * term order; every diagonal entry is stored; columns ascending.  The index map
+ * (ind of eq. findIndices) is the rank in the basis order above, computed
+ * combinatorially instead of with a hash table.  Host arrays, read during the
+ * call.  Errors: TE_ERR_INVALID_ARG (sizes, modes, flags), TE_ERR_NONFINITE,
+ * TE_ERR_UNSUPPORTED (d >= 2^31, a row with more than 256 contributions),
+ * TE_ERR_OOM, TE_ERR_CUDA. */
+te_status te_build_operator(te_ctx* ctx, const te_operator_desc* op, te_matrix** out);
+/* Basis index of an occupation tuple (L int32) of the operator's basis. */
+te_status te_operator_basis_index(const te_operator_desc* op, const int32_t* occ, int64_t* index);
+/* Number operator of one mode over the operator's basis (as te_model_occupation). */
+te_status te_operator_occupation(te_ctx* ctx, const te_operator_desc* op, int32_t mode,
+                                 double* out, uint32_t flags);
+
 /* v_out = exp(-i H t) v_in as te_evolve, plus the states at intermediate times
  * (the extension remarked in Sec. 2.4: inside a step, the restart's H_m and V_m
  * give the state at any time the step covers, so sampling costs no extra

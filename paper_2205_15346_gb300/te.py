@@ -85,6 +85,13 @@ class te_model_desc(C.Structure):
                 ("p", C.POINTER(C.c_double))]
 
 
+class te_operator_desc(C.Structure):
+    _fields_ = [("n_modes", C.c_int32), ("n_particles", C.c_int32),
+                ("max_occ", C.POINTER(C.c_int32)), ("n_terms", C.c_int32),
+                ("term_len", C.POINTER(C.c_int32)), ("modes", C.POINTER(C.c_int32)),
+                ("dagger", C.POINTER(C.c_int32)), ("coef", C.POINTER(C.c_double))]
+
+
 _P = C.c_void_p
 _SIGS = {
     "te_version": (C.c_char_p, []),
@@ -106,6 +113,10 @@ _SIGS = {
     "te_evolve_sampled": (C.c_int32, [_P, _P, _P, C.c_double, C.c_int32, _P, C.c_double,
                                       C.c_int32, C.POINTER(te_options), _P, _P, C.c_int32, _P,
                                       _P, _P, C.POINTER(te_stats)]),
+    "te_build_operator": (C.c_int32, [_P, C.POINTER(te_operator_desc), C.POINTER(_P)]),
+    "te_operator_basis_index": (C.c_int32, [C.POINTER(te_operator_desc), _P, C.POINTER(C.c_int64)]),
+    "te_operator_occupation": (C.c_int32, [_P, C.POINTER(te_operator_desc), C.c_int32, _P,
+                                           C.c_uint32]),
     "te_model_occupation": (C.c_int32, [_P, C.POINTER(te_model_desc), C.c_int32, _P, C.c_uint32]),
     "te_evolve_batch": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_double, C.c_double, C.c_int32,
                                     C.POINTER(te_options), _P, _P, _P]),
@@ -453,6 +464,53 @@ def te_evolve_multi(ctx, Hs, v_ins, ts, tol: float, m: int, opt: te_options | No
                               C.cast(stat, C.c_void_p))
     _check(ctx, s, allow)
     return v_outs, [x.as_dict() for x in sts], [int(x) for x in stat], s
+
+
+def operator_desc(op: dict):
+    """te_operator_desc for {"L", "N", "caps" (or None), "terms": [(coef, [(mode, dagger), ...])]}
+    (the oracle's format); returns (desc, keepalive)."""
+    L, N = int(op["L"]), int(op["N"])
+    terms = op["terms"]
+    tl = np.array([len(f) for _, f in terms], dtype=np.int32)
+    modes = np.array([m for _, f in terms for (m, _) in f] or [0], dtype=np.int32)
+    dag = np.array([int(g) for _, f in terms for (_, g) in f] or [0], dtype=np.int32)
+    coef = np.array([[complex(c).real, complex(c).imag] for c, _ in terms] or [[0.0, 0.0]],
+                    dtype=np.float64).reshape(-1)
+    caps = None if op.get("caps") is None else np.ascontiguousarray(op["caps"], dtype=np.int32)
+    keep = (tl, modes, dag, coef, caps)
+    d = te_operator_desc()
+    d.n_modes, d.n_particles, d.n_terms = L, N, len(terms)
+    d.max_occ = caps.ctypes.data_as(C.POINTER(C.c_int32)) if caps is not None else None
+    d.term_len = tl.ctypes.data_as(C.POINTER(C.c_int32))
+    d.modes = modes.ctypes.data_as(C.POINTER(C.c_int32))
+    d.dagger = dag.ctypes.data_as(C.POINTER(C.c_int32))
+    d.coef = coef.ctypes.data_as(C.POINTER(C.c_double))
+    return d, keep
+
+
+def te_build_operator(ctx, op: dict):
+    desc, keep = operator_desc(op)
+    out = C.c_void_p()
+    _check(ctx, lib().te_build_operator(ctx, C.byref(desc), C.byref(out)))
+    return out
+
+
+def te_operator_basis_index(op: dict, occ) -> int:
+    desc, keep = operator_desc(op)
+    o = np.ascontiguousarray(occ, dtype=np.int32)
+    idx = C.c_int64()
+    s = lib().te_operator_basis_index(C.byref(desc), C.c_void_p(o.ctypes.data), C.byref(idx))
+    if s != TE_OK:
+        raise TEError(s, "invalid occupation tuple")
+    return idx.value
+
+
+def te_operator_occupation(ctx, op: dict, mode: int, d: int):
+    desc, keep = operator_desc(op)
+    out = np.empty(d, dtype=np.float64)
+    _check(ctx, lib().te_operator_occupation(ctx, C.byref(desc), int(mode),
+                                             C.c_void_p(out.ctypes.data), 0))
+    return out
 
 
 def te_model_occupation(ctx, params: dict, mode: int, out=None):
