@@ -41,6 +41,10 @@
 
 namespace {
 
+// threads of the one-CTA-per-vector / per-problem reductions (they add up to tens of
+// thousands of partials each)
+constexpr int kReduceThreads = 1024;
+
 constexpr int kRowsPerWarp = 8;                          // rows of one warp in a chunk
 constexpr int kChunkRows = kRowsPerWarp * (TE_BLOCK / 32);   // rows of one chunk (one CTA task)
 
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_norm_block(const double2* __restri
 // KB0r / KB4r: beta0_b = ||w_b|| opens the next Krylov space (one CTA per vector).
 // init: validation of v_in (Sec. 2.1 assumes ||v(0)|| = 1); otherwise only the
 // vectors whose step kernel took a step in this restart are updated.
-__global__ void __launch_bounds__(TE_BLOCK) k_beta0_block(DevState* st_base, const double* partials,
+__global__ void __launch_bounds__(kReduceThreads) k_beta0_block(DevState* st_base, const double* partials,
                                                           int G, int init) {
     __shared__ double sh[32];
     DevState* st = st_base + blockIdx.x;
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(TE_BLOCK, 3) k_spmm_block(
 }
 
 // KB1r: alpha_b = scale_b[j]^2 Re<u_b, y_b> (one CTA per vector).
-__global__ void __launch_bounds__(TE_BLOCK) k_alpha_block(DevState* st_base, const double* partials,
+__global__ void __launch_bounds__(kReduceThreads) k_alpha_block(DevState* st_base, const double* partials,
                                                           int64_t nchunks, int j) {
     __shared__ double sh[32];
     DevState* st = st_base + blockIdx.x;
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_orth_block(double2* __restrict__ W
 
 // KB2r: h_{j+1,j} = ||w~_b||, the breakdown test of Algorithm 1 step 1 and
 // scale_b[j+1] (one CTA per vector).
-__global__ void __launch_bounds__(TE_BLOCK) k_decide_block(DevState* st_base, const double* partials,
+__global__ void __launch_bounds__(kReduceThreads) k_decide_block(DevState* st_base, const double* partials,
                                                            int G, int j) {
     __shared__ double sh[32];
     DevState* st = st_base + blockIdx.x;
@@ -524,18 +528,18 @@ te_status capture_block_restart(te_ctx* ctx, const te_matrix* H, BlockPlan* p, c
         if (p->profile && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
-        k_alpha_block<<<B, TE_BLOCK, 0, s>>>(p->st, p->partials, p->nchunks, j);
+        k_alpha_block<<<B, kReduceThreads, 0, s>>>(p->st, p->partials, p->nchunks, j);
         k_orth_block<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->V + (size_t)(j + 1) * blk,
                                                          p->V + (size_t)j * blk, p->S, p->d, B,
                                                          p->st, j + 1 < m, p->partials);
-        k_decide_block<<<B, TE_BLOCK, 0, s>>>(p->st, p->partials, p->grid_stream, j);
+        k_decide_block<<<B, kReduceThreads, 0, s>>>(p->st, p->partials, p->grid_stream, j);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = launch_step_batch(p->st, B, m, s);
     if (e == cudaSuccess) {
         k_recombine_block<<<p->grid_stream, TE_BLOCK, sizeof(double2) * B * m, s>>>(
             p->V, p->S, p->d, B, m, p->st, p->partials);
-        k_beta0_block<<<B, TE_BLOCK, 0, s>>>(p->st, p->partials, p->grid_stream, 0);
+        k_beta0_block<<<B, kReduceThreads, 0, s>>>(p->st, p->partials, p->grid_stream, 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -746,7 +750,7 @@ te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const doubl
     if (e == cudaSuccess) {
         k_pack<<<gpk, TE_BLOCK, 0, s>>>(src, d, nvec, B, p->V, p->S);
         k_norm_block<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->V, d, B, p->partials);
-        k_beta0_block<<<B, TE_BLOCK, 0, s>>>(p->st, p->partials, p->grid_stream, 1);
+        k_beta0_block<<<B, kReduceThreads, 0, s>>>(p->st, p->partials, p->grid_stream, 1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)

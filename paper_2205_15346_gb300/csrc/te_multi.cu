@@ -52,6 +52,10 @@ struct MProb {
 
 namespace {
 
+// threads of the one-CTA-per-vector / per-problem reductions (they add up to tens of
+// thousands of partials each)
+constexpr int kReduceThreads = 1024;
+
 constexpr int kChunkElems = 2048;   // elements per chunk of the streaming kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_multi(
 }
 
 // KM1r: alpha_p = scale_p[j]^2 Re<u_p, y_p> (one CTA per problem).
-__global__ void __launch_bounds__(TE_BLOCK) k_alpha_multi(DevState* st, const int64_t* task_start,
+__global__ void __launch_bounds__(kReduceThreads) k_alpha_multi(DevState* st, const int64_t* task_start,
                                                           const double* partials, int j) {
     __shared__ double sh[32];
     DevState* sp = st + blockIdx.x;
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_orth_multi(
 
 // KM2r: h_{j+1,j} of problem p, its breakdown test (Algorithm 1 step 1) and
 // scale_p[j+1].
-__global__ void __launch_bounds__(TE_BLOCK) k_decide_multi(DevState* st, const int64_t* chunk_start,
+__global__ void __launch_bounds__(kReduceThreads) k_decide_multi(DevState* st, const int64_t* chunk_start,
                                                            const double* partials, int j) {
     __shared__ double sh[32];
     DevState* sp = st + blockIdx.x;
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_recombine_multi(
 
 // beta0_p = ||w_p|| opens problem p's next Krylov space (init: validation of
 // v_in, Sec. 2.1 assumes ||v(0)|| = 1).
-__global__ void __launch_bounds__(TE_BLOCK) k_beta0_multi(DevState* st, const int64_t* chunk_start,
+__global__ void __launch_bounds__(kReduceThreads) k_beta0_multi(DevState* st, const int64_t* chunk_start,
                                                           const double* partials, int init) {
     __shared__ double sh[32];
     DevState* sp = st + blockIdx.x;
@@ -397,17 +401,17 @@ te_status capture_multi_round(te_ctx* ctx, MultiPlan* p, cudaStream_t s) {
                                                       p->st, j, p->partials, p->ctr);
         if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
-        k_alpha_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->task_start, p->partials, j);
+        k_alpha_multi<<<n, kReduceThreads, 0, s>>>(p->st, p->task_start, p->partials, j);
         k_orth_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, Y, X, p->S,
                                                          p->st, j, p->partials);
-        k_decide_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->chunk_start, p->partials, j);
+        k_decide_multi<<<n, kReduceThreads, 0, s>>>(p->st, p->chunk_start, p->partials, j);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = launch_step_batch(p->st, n, m, s);
     if (e == cudaSuccess) {
         k_recombine_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, p->V,
                                                               p->S, blk, p->st, 0, p->partials);
-        k_beta0_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->chunk_start, p->partials, 0);
+        k_beta0_multi<<<n, kReduceThreads, 0, s>>>(p->st, p->chunk_start, p->partials, 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -624,7 +628,7 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
     if (e == cudaSuccess) {
         k_recombine_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, p->V,
                                                               p->S, blk, p->st, 1, p->partials);
-        k_beta0_multi<<<n, TE_BLOCK, 0, s>>>(p->st, p->chunk_start, p->partials, 1);
+        k_beta0_multi<<<n, kReduceThreads, 0, s>>>(p->st, p->chunk_start, p->partials, 1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
