@@ -79,24 +79,29 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def k1_source_hash() -> str:
-    """First 16 hex digits of the SHA-256 of the K1 sources (te_sell.cu + te_slices.cuh)."""
+def k1_source_hash(sources=None) -> str:
+    """First 16 hex digits of the SHA-256 of a kernel's sources (default: K1's,
+    te_sell.cu + te_slices.cuh)."""
     h = hashlib.sha256()
-    for f in K1_SOURCES:
+    for f in sources or K1_SOURCES:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per K1 launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def _csrc(*names):
+    return [os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", n) for n in names]
+
+
+def recorded_traffic(summary=PROFILE_SUMMARY, sources=None):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    if not os.path.exists(summary):
         return None
-    txt = open(PROFILE_SUMMARY).read()
+    txt = open(summary).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not b or h.group(1) != k1_source_hash():
+    if not h or not b or h.group(1) != k1_source_hash(sources):
         return None
     return float(b.group(1))
 
@@ -548,7 +553,10 @@ def run_batch(args):
             "batched_over_one_at_a_time": value / (nvec / solo_s),
             "max_diff_over_tol_vs_alone": worst,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
+                         "traffic": recorded_traffic(
+                             os.path.join(ROOT, "profiles", "k_spmm_block_batch_xxzdm_L20_x64.md"),
+                             _csrc("te_block.cu")),
                          "kernel": "k_spmm_block (KB1: Y = s H X - b X_prev per vector, alpha partials)",
                          "flops_per_launch": kb1_flops,
                          "complex_equivalent_tflops": kb1_flops_complex / kb1_avg_s / 1e12,
@@ -688,7 +696,10 @@ def run_multi(args):
             "grouped_over_one_at_a_time": value / (n / solo_s),
             "max_diff_over_tol_vs_alone": worst,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
+                         "traffic": recorded_traffic(
+                             os.path.join(ROOT, "profiles", "k_spmv_multi_tfim_multi_x32.md"),
+                             _csrc("te_multi.cu", "te_slices.cuh")),
                          "kernel": "k_spmv_multi (KM1: grouped SpMV of all running problems)",
                          "avg_launch_ms": spmv_ms / spmv_n,
                          "flops": "executed FP64 work of all grouped SpMV launches / their total time",
