@@ -325,6 +325,7 @@ def run_ours(args):
     p, d, t, tol, m = wl["params"], wl["d"], wl["t"], wl["tol"], wl["m"]
     ctx = te.te_create(local)
     H = te.te_build_model(ctx, p)
+    te.te_matrix_tune(ctx, H)                 # SpMV work-item size, timed on this GPU
     info = te.te_matrix_info_get(H)
     v0 = W.initial_vector(wl["v0"], d, index_of=lambda occ: te.te_model_basis_index(p, occ))
     vin = torch.from_numpy(v0).cuda()
@@ -422,6 +423,7 @@ def run_ours(args):
                          "kernel": (("k_spmv_sellv" if info["sell_dict"] > 0 else "k_spmv_sell") +
                                     " (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)"),
                          "value_table": info["sell_dict"],
+                         "slices_per_task": info["sell_tpt"],
                          "flops_per_launch": k1_flops, "bytes_per_launch": k1_bytes,
                          "complex_equivalent_tflops": k1_flops_complex / k1_avg_s / 1e12,
                          "avg_launch_ms": 1000.0 * k1_avg_s,
@@ -599,6 +601,8 @@ def run_multi(args):
     n = len(probs)
     ctx = te.te_create(local)
     Hs = [te.te_build_model(ctx, q["params"]) for q in probs]
+    for H in Hs:
+        te.te_matrix_tune(ctx, H)
     infos = [te.te_matrix_info_get(H) for H in Hs]
     v0 = [W.random_state(q["v0_seed"], q["d"]) for q in probs]
     vin = [torch.from_numpy(v).cuda() for v in v0]
@@ -742,6 +746,7 @@ def run_sampled(args):
     ts = wl["samples"]
     ctx = te.te_create(local)
     H = te.te_build_model(ctx, p)
+    te.te_matrix_tune(ctx, H)
     L = 2 + p["K"] + p["Kp"]
     occ = torch.stack([te.te_model_occupation(ctx, p, l, out=torch.empty(d, dtype=torch.float64,
                                                                          device="cuda"))
@@ -829,6 +834,7 @@ def run_serve(args):
     pool = []
     for fam, p in W.serve_pool():
         H = te.te_build_model(ctx, p)
+        te.te_matrix_tune(ctx, H)
         pool.append((H, te.te_matrix_info_get(H)["d"], p))
     reqs = W.serve_requests(args.requests)
     m = 40

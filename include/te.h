@@ -132,7 +132,7 @@ typedef struct te_matrix_info {
     int32_t sell_dict;         /* distinct off-diagonal values of a value-indexed copy (column +
                                   16-bit table index per entry, real diagonal apart); 0 when the
                                   copy stores full values (complex diagonal or > 65535 values) */
-    int32_t reserved;
+    int32_t sell_tpt;          /* slices (of 32 rows) per work item of the sliced SpMV */
 } te_matrix_info;
 
 /* Synthetic model Hamiltonians built on the device (Sec. 3: the matrix of an
@@ -222,6 +222,15 @@ te_status te_matrix_export(te_ctx* ctx, const te_matrix* H, int32_t* rowptr, int
 
 /* Free a matrix (and any cached solver plans built for it). */
 void te_matrix_free(te_matrix* H);
+
+/* Autotune the sliced SpMV of H on this GPU: times the product (CUDA events, the
+ * best of `repeats` launches after one warm-up) for work items of 1, 2, 3, 4, 6 and
+ * 8 slices and keeps the fastest (te_matrix_info.sell_tpt).  The initial choice
+ * is a fixed rule (about 1.5K stored entries per item, at most 4 slices).  Cached
+ * solver plans of H are dropped (their scratch depends on the item size); returns
+ * TE_ERR_INVALID_ARG while a solve on H is running.  best_ms (may be NULL)
+ * receives the fastest product time.  repeats: 1..100. */
+te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* best_ms);
 
 /* ---- products and solves ------------------------------------------------ */
 

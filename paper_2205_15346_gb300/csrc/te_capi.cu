@@ -700,6 +700,7 @@ te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
     info->spmv_lanes = H->lanes;
     info->sell_nnz = H->sell_nnz;
     info->sell_dict = H->dict_n;
+    info->sell_tpt = H->sell_tpt;
     return TE_OK;
 }
 
@@ -740,6 +741,76 @@ void te_matrix_free(te_matrix* H) {
                     (void*)H->m3})
         if (q) cudaFree(q);
     delete H;
+}
+
+te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* best_ms) {
+    if (!ctx || !H || repeats < 1 || repeats > 100) return TE_ERR_INVALID_ARG;
+    enter(ctx);
+    if (te_status js = join_user_stream(ctx)) return js;
+    // cached plans size their scratch for the current item size: drop them first
+    if (multi_plans_in_use(ctx, H->id))
+        return set_error(ctx, TE_ERR_INVALID_ARG, "a grouped solve on this matrix is running");
+    {
+        std::vector<Plan*> drop;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            for (Plan* p : ctx->plans)
+                if (p->matrix_id == H->id && p->in_use)
+                    return set_error(ctx, TE_ERR_INVALID_ARG, "a solve on this matrix is running");
+            auto it = std::partition(ctx->plans.begin(), ctx->plans.end(),
+                                     [&](Plan* p) { return p->matrix_id != H->id; });
+            drop.assign(it, ctx->plans.end());
+            ctx->plans.erase(it, ctx->plans.end());
+        }
+        cudaStreamSynchronize(ctx->stream);
+        for (Plan* p : drop) free_plan(p);
+        multi_plans_release(ctx, H->id);
+    }
+    cudaStream_t s = ctx->stream;
+    const int64_t d = H->d;
+    const int cand[] = {1, 2, 3, 4, 6, 8};
+    const int keep = H->sell_tpt;
+    H->sell_tpt = 1;                                  // the largest scratch any candidate needs
+    const int64_t np = sell_partials(H);
+    H->sell_tpt = keep;
+    double2* x = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&x, sizeof(double2) * 2 * (size_t)d + sizeof(double) * ((size_t)d + np));
+    if (e != cudaSuccess) return cuda_error(ctx, e, "te_matrix_tune scratch");
+    double2* y = x + d;
+    double* xsum = reinterpret_cast<double*>(y + d);
+    double* parts = xsum + d;
+    e = cudaMemsetAsync(x, 0, sizeof(double2) * 2 * (size_t)d + sizeof(double) * ((size_t)d + np), s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = INFINITY;
+    int best_tpt = keep;
+    for (int c : cand) {
+        if (e != cudaSuccess) break;
+        if (c > 1 && (H->nslices + c - 1) / c < 4) break;     // too few items to matter
+        H->sell_tpt = c;
+        double tmin = INFINITY;
+        for (int r = 0; r <= repeats && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_spmv_sell(H, x, xsum, nullptr, y, ctx->spmv_st, 0, 1, parts, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && r > 0) tmin = std::min(tmin, (double)ms);   // r = 0 warms up
+        }
+        if (e == cudaSuccess && tmin < best) {
+            best = tmin;
+            best_tpt = c;
+        }
+    }
+    H->sell_tpt = (e == cudaSuccess) ? best_tpt : keep;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "te_matrix_tune");
+    if (best_ms) *best_ms = best;
+    return TE_OK;
 }
 
 // ------------------------------------------------------------------ products and solves

@@ -263,6 +263,7 @@ cudaError_t launch_observables(const double2* W, int64_t d, int ns, const double
 
 // grouped independent solves (te_multi.cu)
 void multi_plans_release(te_ctx* ctx, uint64_t matrix_id);    // matrix_id 0: all of ctx
+bool multi_plans_in_use(te_ctx* ctx, uint64_t matrix_id);
 te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const double* const* v_in,
                           const double* t, double tol, int m, const te_options& o,
                           double* const* v_out, bool dev, te_stats* stats, int32_t* status,

@@ -549,6 +549,16 @@ te_status acquire_multi_plan(te_ctx* ctx, int n, const te_matrix* const* H, int 
 
 }  // namespace
 
+// A grouped solve that uses the matrix is running.
+bool multi_plans_in_use(te_ctx* ctx, uint64_t matrix_id) {
+    std::lock_guard<std::mutex> lk(g_multi_mu);
+    for (MultiPlan* q : g_multi_plans)
+        if (q->ctx == ctx && q->in_use &&
+            std::find(q->ids.begin(), q->ids.end(), matrix_id) != q->ids.end())
+            return true;
+    return false;
+}
+
 // Drop the grouped plans of a context (matrix_id 0) or those that use one matrix.
 void multi_plans_release(te_ctx* ctx, uint64_t matrix_id) {
     std::vector<MultiPlan*> drop;

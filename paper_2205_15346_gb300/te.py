@@ -75,7 +75,7 @@ class te_stats(C.Structure):
 class te_matrix_info(C.Structure):
     _fields_ = [("d", C.c_int64), ("nnz", C.c_int64), ("norm1", C.c_double),
                 ("max_row_nnz", C.c_int32), ("spmv_lanes", C.c_int32), ("sell_nnz", C.c_int64),
-                ("sell_dict", C.c_int32), ("reserved", C.c_int32)]
+                ("sell_dict", C.c_int32), ("sell_tpt", C.c_int32)]
 
 
 class te_model_desc(C.Structure):
@@ -106,6 +106,7 @@ _SIGS = {
     "te_matrix_info_get": (C.c_int32, [_P, C.POINTER(te_matrix_info)]),
     "te_matrix_export": (C.c_int32, [_P, _P, _P, _P, _P, C.c_uint32]),
     "te_matrix_free": (None, [_P]),
+    "te_matrix_tune": (C.c_int32, [_P, _P, C.c_int32, C.POINTER(C.c_double)]),
     "te_spmv": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_spmv_noalloc": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
@@ -327,6 +328,13 @@ def te_matrix_export(ctx, H):
     _check(ctx, lib().te_matrix_export(ctx, H, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data),
                                        C.c_void_p(val.ctypes.data), 0))
     return rp, col, val
+
+
+def te_matrix_tune(ctx, H, repeats: int = 5) -> float:
+    """Autotune H's sliced SpMV on this GPU; returns the best product time (ms)."""
+    best = C.c_double()
+    _check(ctx, lib().te_matrix_tune(ctx, H, int(repeats), C.byref(best)))
+    return best.value
 
 
 def te_matrix_free(H) -> None:

@@ -130,3 +130,23 @@ def test_model_matrices_use_value_table(te, ctx, params):
         assert te.te_matrix_info_get(H)["sell_dict"] > 0
     finally:
         te.te_matrix_free(H)
+
+
+def test_autotune_keeps_the_product_and_solves_exact(te, ctx):
+    """te_matrix_tune only changes how work is split: the product stays within
+    the bound above and a solve after tuning still matches the oracle."""
+    from oracle import krylov
+    p = W.xxzdm_params(12, 7)
+    A = models.build(p).to_scipy()
+    H = te.te_build_model(ctx, p)
+    try:
+        v0 = W.random_state(8, A.shape[0])
+        te.te_evolve(ctx, H, v0, 2.0, 1e-9, 20)          # a cached plan exists before tuning
+        ms = te.te_matrix_tune(ctx, H, 3)
+        info = te.te_matrix_info_get(H)
+        assert ms > 0 and info["sell_tpt"] in (1, 2, 3, 4, 6, 8)
+        check_spmv(te, ctx, H, A, 16)
+        out, st, _ = te.te_evolve(ctx, H, v0, 2.0, 1e-9, 20)
+        assert np.linalg.norm(out - krylov.evolve(A, v0, 2.0, 1e-9, 20).v) <= 2e-9 + 1e-12
+    finally:
+        te.te_matrix_free(H)
