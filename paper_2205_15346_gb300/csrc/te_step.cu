@@ -123,40 +123,87 @@ __device__ __forceinline__ double f_eig(const Small& F, double tau) {
 
 // f(tau) by the Chebyshev expansion: |sum_k c_k (-i)^k J_k(a tau) g_k| with
 // J_k from Miller's backward recurrence J_{k-1} = (2k / z) J_k - J_{k+1},
-// started at F.M with J_{M+1} = 0 and normalised by J_0 + 2 sum J_{2k} = 1.
-// The loop length is the same in every lane (F.M), so warps never diverge.
+// started at M = K(z) + kMillerExtra with J_{M+1} = 0 (K(z) terms for this
+// node's own argument z, at most the integral's F.K) and normalised by
+// J_0 + 2 sum J_{2k} = 1.  Every FP64 instruction of a warp occupies the FP64
+// pipe for ~64 cycles on GB300, so the loop is written for few of them: the
+// weights c_k = 2 (k > 0) and the factor 2 of the normalisation are applied
+// once at the end, the (-i)^k pattern is unrolled by four, and (for z >= 1,
+// where one step grows J by at most 2M/z <= 2M) the overflow guard runs once per
+// four steps.  Nodes with z < 1 take the same recurrence with a guard per step.
 __device__ __forceinline__ double f_cheb(const Small& F, double tau) {
     const double z = F.a * tau;
     const int first = F.n - 1;       // g_k = 0 below this index
     if (!(z > 1e-300)) return first == 0 ? F.h * fabs(F.g[0]) : 0.0;
+    const int Kn = min(bessel_terms(z), F.K);
+    const int M = Kn + kMillerExtra;
     const double inv = 2.0 / z;
-    double t = inv * F.M;            // 2k / z for the current k
+    double t = inv * M;              // 2k / z for the current k
     double jp = 0.0, jc = 1e-300;    // J_{k+1}, J_k (unnormalised)
-    double S = 0.0, re = 0.0, im = 0.0;
-    for (int k = F.M; k >= 0; --k) {
-        if (k >= first && k <= F.K) {
-            const double c = (k == 0 ? 1.0 : 2.0) * F.g[k] * jc;
-            switch (k & 3) {
-                case 0: re += c; break;
-                case 1: im -= c; break;
-                case 2: re -= c; break;
-                default: im += c; break;
-            }
-        }
-        if ((k & 1) == 0) S += (k == 0) ? jc : 2.0 * jc;
-        if (k == 0) break;
-        const double jn = fma(t, jc, -jp);
-        jp = jc;
-        jc = jn;
-        t -= inv;
-        if (fabs(jc) > kBig) {
-            jc *= kSmall;
-            jp *= kSmall;
-            S *= kSmall;
-            re *= kSmall;
-            im *= kSmall;
-        }
+    double S2 = 0.0, re = 0.0, im = 0.0, j0 = 0.0;
+    const double* g = F.g;
+    // one step at index k: accumulate, then move to k - 1
+#define TE_ACC(k, q)                                                       \
+    if ((k) >= first && (k) <= Kn) {                                        \
+        if ((q) == 0) re = fma(g[k], jc, re);                               \
+        else if ((q) == 1) im = fma(-g[k], jc, im);                         \
+        else if ((q) == 2) re = fma(-g[k], jc, re);                         \
+        else im = fma(g[k], jc, im);                                        \
+    }                                                                       \
+    if (((q) & 1) == 0) S2 += jc;
+#define TE_REC()                                                           \
+    {                                                                       \
+        const double jn = fma(t, jc, -jp);                                  \
+        jp = jc;                                                            \
+        jc = jn;                                                            \
+        t -= inv;                                                           \
     }
+#define TE_GUARD()                                                         \
+    if (fabs(jc) > kBig) {                                                  \
+        jc *= kSmall;                                                       \
+        jp *= kSmall;                                                       \
+        S2 *= kSmall;                                                       \
+        re *= kSmall;                                                       \
+        im *= kSmall;                                                       \
+    }
+    int k = M;
+    if (z < 1.0) {
+        for (; k >= 0; --k) {
+            const int q = k & 3;
+            TE_ACC(k, q)
+            if (k == 0) break;
+            TE_REC()
+            TE_GUARD()
+        }
+        j0 = jc;
+    } else {
+        for (; (k & 3) != 3; --k) {             // down to the next k = 3 (mod 4)
+            const int q = k & 3;
+            TE_ACC(k, q)
+            TE_REC()
+        }
+        TE_GUARD()
+        for (; k >= 3; k -= 4) {
+            TE_ACC(k, 3)
+            TE_REC()
+            TE_ACC(k - 1, 2)
+            TE_REC()
+            TE_ACC(k - 2, 1)
+            TE_REC()
+            TE_ACC(k - 3, 0)
+            if (k == 3) break;                  // J_0 reached
+            TE_REC()
+            TE_GUARD()
+        }
+        j0 = jc;
+    }
+#undef TE_ACC
+#undef TE_REC
+#undef TE_GUARD
+    // sum_k c_k (...) = 2 sum_k (...) - [k = 0 term];  J_0 + 2 sum J_2k = 2 S2 - J_0
+    re = 2.0 * re - (first == 0 ? g[0] * j0 : 0.0);
+    im = 2.0 * im;
+    const double S = 2.0 * S2 - j0;
     // hypot: the unnormalised sums can be near 1e-215, where re * re underflows
     return F.h * hypot(re, im) / fabs(S);
 }
