@@ -212,6 +212,12 @@ __device__ __forceinline__ double f_at(const Small& F, double tau) {
     return F.method == TE_SMALLEXP_EIG ? f_eig(F, tau) : f_cheb(F, tau);
 }
 
+// Unit tanh-sinh nodes of levels 0..kTabLevels-1 on [-1, 1] (x = tanh(pi/2 sinh u),
+// w = pi/2 cosh u / cosh^2(pi/2 sinh u)), in the order the levels visit them.
+constexpr int kTabLevels = 6;
+constexpr int kTabNodes = 201;       // 7 + 6 + 12 + 26 + 50 + 100
+__constant__ int kTabOff[kTabLevels + 1] = {0, 7, 13, 25, 51, 101, 201};
+
 struct Quad {
     int method;
     double rel_tol;
@@ -219,7 +225,31 @@ struct Quad {
     int gauss_n;
     const double* gx;
     const double* gw;
+    const double* tx;                // unit nodes and weights of the first levels
+    const double* tw;
+    double* vals;                    // kTabNodes scratch doubles
 };
+
+// The u of node i of level `level` (same order as the level loops below).
+__device__ __forceinline__ double ts_u(int level, int i) {
+    if (level == 0) return (double)(i - (int)floor(kUMax));
+    const double step = ldexp(1.0, -level);
+    const int kmax = (int)floor((kUMax / step - 1.0) * 0.5);
+    return (2.0 * (i - (kmax + 1)) + 1.0) * step;
+}
+
+// Fill the unit node table (one thread per node).
+__device__ void ts_table(double* tx, double* tw) {
+    for (int i = threadIdx.x; i < kTabNodes; i += blockDim.x) {
+        int level = 0;
+        while (i >= kTabOff[level + 1]) ++level;
+        const double u = ts_u(level, i - kTabOff[level]);
+        const double sv = kHalfPi * sinh(u);
+        const double ch = cosh(sv);
+        tx[i] = tanh(sv);
+        tw[i] = kHalfPi * cosh(u) / (ch * ch);
+    }
+}
 
 // Chebyshev vectors v_k = T_k(T~) e_1 (three buffers rotated in shared memory),
 // extended until g is valid up to index K.
@@ -270,29 +300,47 @@ __device__ double integrate(const Small& F, const Quad& Qd, double a, double b, 
         x = c + r * tanh(s);
         w = r * kHalfPi * cosh(u) / (ch * ch);
     };
-    double loc = 0.0;
-    const int j0 = (int)floor(kUMax);
-    for (int i = tid; i < 2 * j0 + 1; i += nt) {
-        double x, w;
-        node((double)(i - j0), x, w);
-        loc += w * f_at(F, x);
+    // Levels 0..kMinLevel are always needed: their nodes are evaluated in one
+    // parallel round (each level's dependent chains used to run one after another),
+    // then the trapezoid estimates are refined level by level as before.
+    const int n0 = kTabOff[kMinLevel + 1];
+    for (int i = tid; i < n0; i += nt) Qd.vals[i] = r * Qd.tw[i] * f_at(F, c + r * Qd.tx[i]);
+    __syncthreads();
+    if (tid <= kMinLevel) {                              // per-level sums in node order
+        double sum = 0.0;
+        for (int i = kTabOff[tid]; i < kTabOff[tid + 1]; ++i) sum += Qd.vals[i];
+        red[tid] = sum;
     }
-    double total = block_sum_all(loc, red);
-    if (tid == 0) *nodes += 2 * j0 + 1;
+    __syncthreads();
+    double lsum[kMinLevel + 1];
+    for (int l = 0; l <= kMinLevel; ++l) lsum[l] = red[l];
+    __syncthreads();
+    if (tid == 0) *nodes += n0;
+    double total = lsum[0];
     double step = 1.0;
     for (int level = 1; level <= Qd.max_levels; ++level) {
         step *= 0.5;
-        const int kmax = (int)floor((kUMax / step - 1.0) * 0.5);
-        const int count = 2 * (kmax + 1);
-        loc = 0.0;
-        for (int i = tid; i < count; i += nt) {
-            const int k = i - (kmax + 1);
-            double x, w;
-            node((2.0 * k + 1.0) * step, x, w);
-            loc += w * f_at(F, x);
+        double s;
+        if (level <= kMinLevel) {
+            s = lsum[level];
+        } else {
+            const int kmax = (int)floor((kUMax / step - 1.0) * 0.5);
+            const int count = 2 * (kmax + 1);
+            double loc = 0.0;
+            if (level < kTabLevels) {
+                const int o = kTabOff[level];
+                for (int i = tid; i < count; i += nt) loc += r * Qd.tw[o + i] * f_at(F, c + r * Qd.tx[o + i]);
+            } else {
+                for (int i = tid; i < count; i += nt) {
+                    const int k = i - (kmax + 1);
+                    double x, w;
+                    node((2.0 * k + 1.0) * step, x, w);
+                    loc += w * f_at(F, x);
+                }
+            }
+            s = block_sum_all(loc, red);
+            if (tid == 0) *nodes += count;
         }
-        const double s = block_sum_all(loc, red);
-        if (tid == 0) *nodes += count;
         const double nt_total = 0.5 * total + step * s;
         if (level >= kMinLevel && fabs(nt_total - total) <= Qd.rel_tol * fabs(nt_total))
             return nt_total;
@@ -318,6 +366,9 @@ struct Layout {
     double* v3;      // 3 * mcap: Chebyshev vectors
     double* g;       // kKcap: g_k
     double* jk;      // kKcap: J_k for omega
+    double* tx;      // kTabNodes: unit tanh-sinh nodes
+    double* tw;      // kTabNodes: their weights
+    double* tv;      // kTabNodes: weighted integrand values of one round
     int* ri;         // mcap
 };
 
@@ -340,6 +391,9 @@ __device__ Layout carve(double* smem, int mcap, int method) {
     L.rs = p; p += mcap;
     L.al = p; p += mcap;
     L.be = p; p += mcap;
+    L.tx = p; p += kTabNodes;
+    L.tw = p; p += kTabNodes;
+    L.tv = p; p += kTabNodes;
     if (method == TE_SMALLEXP_EIG) {
         L.v3 = L.g = L.jk = nullptr;
     } else {
@@ -520,7 +574,12 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
     const double T = st->T, t_now = st->t_now;
     const double t_rem = T - t_now;
     const double tol_rate = st->tol_rate;
-    Quad Qd{st->quad, st->quad_rel_tol, st->quad_max_levels, st->gauss_n, st->gx, st->gw};
+    Quad Qd{st->quad, st->quad_rel_tol, st->quad_max_levels, st->gauss_n, st->gx, st->gw,
+            L.tx, L.tw, L.tv};
+    if (Qd.method != TE_QUAD_GAUSS) {
+        ts_table(L.tx, L.tw);
+        __syncthreads();
+    }
     int n_integrals = 0;
     // E over [lo_t, hi_t]; for the Chebyshev route first make sure g covers the
     // largest argument a * hi_t (an integral that would need more than kKcap terms
@@ -645,9 +704,11 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
 }  // namespace
 
 int step_smem_bytes(int m) {
-    const size_t eig = sizeof(double2) * 2 * m + sizeof(double) * ((size_t)m * m + 8 * (size_t)m) +
+    const size_t eig = sizeof(double2) * 2 * m +
+                       sizeof(double) * ((size_t)m * m + 8 * (size_t)m + 3 * kTabNodes) +
                        sizeof(int) * m;
-    const size_t cheb = sizeof(double2) * 2 * m + sizeof(double) * (11 * (size_t)m + 2 * kKcap) +
+    const size_t cheb = sizeof(double2) * 2 * m +
+                        sizeof(double) * (11 * (size_t)m + 2 * kKcap + 3 * kTabNodes) +
                         sizeof(int) * m;
     return (int)(eig > cheb ? eig : cheb);
 }
