@@ -72,7 +72,8 @@ typedef int32_t te_status;
 #define TE_SMALLEXP_CHEB 0         /* Chebyshev/Bessel (Jacobi-Anger) series of the tridiagonal H_m (default) */
 #define TE_SMALLEXP_EIG  1         /* diagonalisation of H_m, the paper's choice (Sec. 2.4) */
 /* te_options.flags */
-#define TE_OPT_PROFILE 0x10u       /* time every fused SpMV launch with CUDA events (te_stats.spmv_*) */
+#define TE_OPT_PROFILE 0x10u       /* time the fused SpMV of Lanczos step m/2 of every restart with
+                                      CUDA events (te_stats.spmv_*; one event pair per restart) */
 
 /*
  * Solver options.  te_default_options fills the defaults, which follow the
@@ -113,8 +114,8 @@ typedef struct te_stats {
     double   norm_in;          /* ||v_in|| */
     uint32_t flags;            /* TE_WARN_*, TE_FLAG_* */
     int32_t  m_used;           /* Krylov dimension used (min(m, d)) */
-    double   spmv_ms;          /* TE_OPT_PROFILE: summed CUDA-event time of fused SpMV launches */
-    int64_t  spmv_launches;    /* TE_OPT_PROFILE: launches summed in spmv_ms */
+    double   spmv_ms;          /* TE_OPT_PROFILE: summed CUDA-event time of the timed SpMV launches */
+    int64_t  spmv_launches;    /* TE_OPT_PROFILE: launches summed in spmv_ms (one per restart) */
     double   solve_ms;         /* host wall time of the call */
     int64_t  quad_integrals;   /* error integrals evaluated by the step search */
     int64_t  quad_nodes;       /* integrand evaluations in those integrals */

@@ -523,10 +523,11 @@ te_status capture_block_restart(te_ctx* ctx, const te_matrix* H, BlockPlan* p, c
     TE_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < m && e == cudaSuccess; ++j) {
-        if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j], s, cudaEventRecordExternal);
+        const bool timed = p->profile && j == m / 2;     // one product per round is timed
+        if (timed) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_spmm(H, p, j, s);
-        if (p->profile && e == cudaSuccess)
-            e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
+        if (timed && e == cudaSuccess)
+            e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
         k_alpha_block<<<B, kReduceThreads, 0, s>>>(p->st, p->partials, p->nchunks, j);
         k_orth_block<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->V + (size_t)(j + 1) * blk,
@@ -611,7 +612,7 @@ te_status create_block_plan(te_ctx* ctx, const te_matrix* H, int m, int B, int p
         return set_error(ctx, TE_ERR_CUDA, "preparing the batched workspace");
     }
     if (profile) {
-        p->ev.resize(2 * (size_t)m);
+        p->ev.resize(2);
         for (auto& ev : p->ev) cudaEventCreate(&ev);
     }
     te_status st = capture_block_restart(ctx, H, p, s);
@@ -770,14 +771,12 @@ te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const doubl
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(e, "batched restart");
         if (profile) {
-            for (int j = 0; j < m; ++j) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, p->ev[2 * j], p->ev[2 * j + 1]) == cudaSuccess) {
-                    spmv_ms += ms;
-                    spmv_launches += 1;
-                } else {
-                    cudaGetLastError();
-                }
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) {
+                spmv_ms += ms;
+                spmv_launches += 1;
+            } else {
+                cudaGetLastError();
             }
         }
     }

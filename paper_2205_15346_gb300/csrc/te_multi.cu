@@ -395,11 +395,12 @@ te_status capture_multi_round(te_ctx* ctx, MultiPlan* p, cudaStream_t s) {
         const double2* X = p->V + (size_t)j * blk;
         const double2* Xp = j > 0 ? p->V + (size_t)(j - 1) * blk : nullptr;
         double2* Y = p->V + (size_t)(j + 1) * blk;
-        if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j], s, cudaEventRecordExternal);
+        const bool timed = p->profile && j == m / 2;     // one product per round is timed
+        if (timed) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
         k_spmv_multi<<<p->grid_spmv, TE_BLOCK, 0, s>>>(p->probs, p->task_start, n, X, p->S, Xp, Y,
                                                       p->st, j, p->partials, p->ctr);
-        if (p->profile) e = cudaEventRecordWithFlags(p->ev[2 * j + 1], s, cudaEventRecordExternal);
+        if (timed) e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
         k_alpha_multi<<<n, kReduceThreads, 0, s>>>(p->st, p->task_start, p->partials, j);
         k_orth_multi<<<p->grid_stream, TE_BLOCK, 0, s>>>(p->probs, p->chunk_start, n, Y, X, p->S,
@@ -498,7 +499,7 @@ te_status create_multi_plan(te_ctx* ctx, int n, const te_matrix* const* H, int m
                          std::string("allocating the grouped workspace: ") + cudaGetErrorString(e));
     }
     if (profile) {
-        p->ev.resize(2 * (size_t)m);
+        p->ev.resize(2);
         for (auto& ev : p->ev) cudaEventCreate(&ev);
     }
     te_status st = capture_multi_round(ctx, p, s);
@@ -659,14 +660,12 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
         if (e != cudaSuccess) return fail(e, "grouped restart round");
         ++rounds;
         if (profile) {
-            for (int j = 0; j < m; ++j) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, p->ev[2 * j], p->ev[2 * j + 1]) == cudaSuccess) {
-                    spmv_ms += ms;
-                    spmv_launches += 1;
-                } else {
-                    cudaGetLastError();
-                }
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) {
+                spmv_ms += ms;
+                spmv_launches += 1;
+            } else {
+                cudaGetLastError();
             }
         }
     }
