@@ -172,7 +172,12 @@ def oracle_matrix(wl):
 
 
 def single_view(wl):
-    """The one-vector workload behind a batched one (its first vector)."""
+    """The one-vector workload behind a batched one (its first vector), or the
+    K = K' = 10 size of the runtime study."""
+    if "sizes" in wl:
+        q = wl["sizes"][3]
+        return {"name": "memory_K10", "params": q["params"], "d": q["d"], "v0": q["v0"],
+                "t": wl["t"], "m": wl["m"], "tol": wl["tol"]}
     if "nvec" not in wl:
         return wl
     v = dict(wl)
@@ -285,6 +290,8 @@ DESCRIBE = {
                             "XXZ-DM chain L=20 periodic, d=1048576, nnz=11534336"),
     "memory_K10_sampled": ("the paper's example system at its benchmark size (d=1565904) with "
                            "all 22 mode occupations sampled at 100 times (Sec. 2.4, Sec. 5)"),
+    "memory_scaling": ("the paper's runtime-vs-dimension study (Sec. 5): its example system at "
+                       "K=K'=4,6,8,10 (Nm=K/2, N0=Nc=100) and K=K'=10, N0=Nc=139, t=10"),
     "tfim_multi_x32": ("32 independent open TFIM chains, L uniform on 10..20 (total d=9182208), "
                        "t ~ U[1,20], random v0"),
 }
@@ -829,6 +836,68 @@ def run_sampled(args):
     return 0
 
 
+# The paper's fit of its single-thread CPU runtime, t = a d^b (Sec. 5).
+PAPER_FIT_A, PAPER_FIT_B = 8.1e-6, 1.23
+
+
+def run_scaling(args):
+    """Solve time against the dimension for the sizes of the paper's runtime study,
+    beside the paper's fitted CPU times (context: other hardware)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2205_15346_gb300 import te
+    wl = W.workload(args.workload)
+    t, tol, m = wl["t"], wl["tol"], wl["m"]
+    ctx = te.te_create(local)
+    rows = []
+    with ClockSampler(local) as clk:
+        for q in wl["sizes"]:
+            p, d = q["params"], q["d"]
+            H = te.te_build_model(ctx, p)
+            te.te_matrix_tune(ctx, H)
+            v0 = W.initial_vector(q["v0"], d, index_of=lambda o: te.te_model_basis_index(p, o))
+            vin = torch.from_numpy(v0).cuda()
+            vout = torch.empty_like(vin)
+            for _ in range(args.warmup):
+                te.te_evolve(ctx, H, vin, t, tol, m, v_out=vout)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(args.steps):
+                _, st, _ = te.te_evolve(ctx, H, vin, t, tol, m, v_out=vout)
+            ev1.record()
+            torch.cuda.synchronize()
+            sec = ev0.elapsed_time(ev1) / 1000.0 / args.steps
+            fit = PAPER_FIT_A * d ** PAPER_FIT_B
+            rows.append({"K": p["K"], "N0": p["N0"], "d": d, "nnz": te.te_matrix_info_get(H)["nnz"],
+                         "gpu_s_per_solve": sec, "paper_fit_cpu_s": fit, "ratio_to_fit": fit / sec,
+                         "restarts": st["restarts"], "err_bound": st["err_bound"]})
+            te.te_matrix_free(H)
+    te.te_destroy(ctx)
+    # the GPU's own power law over the four fitted sizes
+    xs = np.log([r["d"] for r in rows[:4]])
+    ys = np.log([r["gpu_s_per_solve"] for r in rows[:4]])
+    b, loga = np.polyfit(xs, ys, 1)
+    k10 = rows[3]
+    line = {
+        "metric": METRIC, "mode": "scaling", "value": 1.0 / k10["gpu_s_per_solve"], "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * k10["gpu_s_per_solve"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (1.0 / k10["gpu_s_per_solve"]) / PAPER_SOLVES_PER_S["memory_K10"],
+        "dtype": "complex128", "data": "the paper's example system (deterministic parameters, Sec. 5)",
+        "config": {"workload": f"{wl['name']}: {DESCRIBE[wl['name']]}, m={m}, tol={tol}",
+                   "value_is": "solves/s at K=K'=10, N0=Nc=100 (d=1565904)"},
+        "sizes": rows,
+        "gpu_fit": {"a": float(np.exp(loga)), "b": float(b)},
+        "paper_fit": {"a": PAPER_FIT_A, "b": PAPER_FIT_B, "hardware": "i9-9900K, 1 thread"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Serving: a Poisson stream of mixed requests through te_submit / te_poll,
     against the same requests solved one at a time (te_evolve)."""
@@ -939,6 +1008,8 @@ def main():
         return run_multi(args)
     if "samples" in W.workload(args.workload):
         return run_sampled(args)
+    if "sizes" in W.workload(args.workload):
+        return run_scaling(args)
     return run_ours(args)
 
 

@@ -161,6 +161,16 @@ def workload(name: str) -> dict:
             probs.append({"params": tfim_params(L, seed=800 + i), "d": 1 << L,
                           "t": float(1.0 + 19.0 * u[2 * i + 1]), "v0_seed": 900 + i})
         return {"name": name, "problems": probs, "m": 30, "tol": 1e-8}
+    if name == "memory_scaling":
+        # the sizes of the paper's runtime study (Sec. 5): K = K' = 4, 6, 8, 10, Nm = K / 2,
+        # N0 = Nc = 100, t = 10, and the memory-limit point K = K' = 10, N0 = Nc = 139
+        sizes = [(K, 100) for K in (4, 6, 8, 10)] + [(10, 139)]
+        probs = []
+        for K, N0 in sizes:
+            p = memory_params(K=K, Kp=K, N0=N0, Nm=K // 2, Nc=float(N0))
+            probs.append({"params": p, "d": memory_dim(p),
+                          "v0": ("occupation", memory_initial_occupation(p))})
+        return {"name": name, "sizes": probs, "t": 10.0, "m": 40, "tol": 1e-7}
     if name == "memory_K10_sampled":
         # the same solve with every mode occupation at 100 evenly spaced times
         w = workload("memory_K10")
