@@ -77,8 +77,9 @@ void free_plan(Plan* p) {
 }
 
 size_t plan_bytes(int64_t d, int m, int reorth, int max_grid) {
-    size_t b = sizeof(double2) * (size_t)(m + 1) * (size_t)d + sizeof(double) * (size_t)d +
-               sizeof(DevState) + sizeof(double) * (size_t)max_grid;
+    size_t b = sizeof(double2) * (size_t)(m + 1) * (size_t)d +
+               sizeof(double) * (size_t)(m + 1) * (size_t)d + sizeof(DevState) +
+               sizeof(double) * (size_t)max_grid;
     if (reorth) b += sizeof(double) * (size_t)max_grid * TE_M_MAX * 2;
     return b;
 }
@@ -94,33 +95,35 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         const double2* x = p->V + (size_t)j * d;
         const double2* xprev = j > 0 ? p->V + (size_t)(j - 1) * d : nullptr;
         double2* y = p->V + (size_t)(j + 1) * d;
+        double* sj1 = p->S ? p->S + (size_t)(j + 1) * d : nullptr;   // Re + Im of column j + 1
         // external event nodes: plain records inside a capture only order work
         const bool timed = p->profile && j == m / 2;     // one product per restart is timed
         if (timed) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
         if (e == cudaSuccess)
             e = p->lanes ? launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
                                                p->grid_k1, s)
-                         : launch_spmv_sell(H, x, p->S, xprev, y, p->st, j, 0, p->partials, s);
+                         : launch_spmv_sell(H, x, p->S + (size_t)j * d, xprev, y, p->st, j, 0,
+                                            p->partials, s);
         if (timed && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
         if (p->reorth) {
-            e = launch_orth_norm(y, p->S, x, d, p->st, j, 1, 0, p->partials, p->grid_stream, s);
+            e = launch_orth_norm(y, sj1, x, d, p->st, j, 1, 0, p->partials, p->grid_stream, s);
             for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
                 e = launch_reorth_dots(p->V, y, d, p->st, j, p->partials_r, p->grid_reorth, s);
                 if (e == cudaSuccess)
-                    e = launch_reorth_update(p->V, y, p->S, d, p->st, j, pass == 1, p->partials,
+                    e = launch_reorth_update(p->V, y, sj1, d, p->st, j, pass == 1, p->partials,
                                              p->grid_stream, s);
             }
         } else {
-            e = launch_orth_norm(y, p->S, x, d, p->st, j, j + 1 < m, 1, p->partials,
+            e = launch_orth_norm(y, sj1, x, d, p->st, j, j + 1 < m, 1, p->partials,
                                  p->grid_stream, s);
         }
     }
     if (e == cudaSuccess) e = launch_step(p->st, m, s);
     if (e == cudaSuccess && p->ns > 0)
         e = launch_sample_kernels(p->st, p->samp_ts, p->ns, m, p->samp_coef, p->samp_bound, p->V,
-                                  d, p->samp_buf, p->grid_stream, s);
+                                  p->S, d, p->samp_buf, p->grid_stream, s);
     if (e == cudaSuccess)
         e = launch_recombine(p->V, p->S, d, p->st, p->partials, p->grid_stream, s);
     if (e == cudaSuccess)
@@ -156,7 +159,9 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
                                                 lanes ? 0 : sell_partials(H));
     p->bytes = plan_bytes(H->d, m, reorth, max_grid);
     cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
-    if (e == cudaSuccess && lanes == 0) e = cudaMalloc(&p->S, sizeof(double) * (size_t)H->d);
+    // Re + Im of every Krylov column (the sliced SpMV and the recombination read them)
+    if (e == cudaSuccess && lanes == 0)
+        e = cudaMalloc(&p->S, sizeof(double) * (size_t)(m + 1) * (size_t)H->d);
     if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * (size_t)max_grid);
     if (e == cudaSuccess && reorth)

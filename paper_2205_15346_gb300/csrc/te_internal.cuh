@@ -254,8 +254,8 @@ te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const doubl
 int sample_omega_smem(int mcap);
 cudaError_t sample_prepare();
 cudaError_t launch_sample_kernels(DevState* st, const double* ts, int ns, int mcap, double2* coef,
-                                  double* bound, const double2* V, int64_t d, double2* out,
-                                  int grid_stream, cudaStream_t s);
+                                  double* bound, const double2* V, const double* S, int64_t d,
+                                  double2* out, int grid_stream, cudaStream_t s);
 cudaError_t launch_gather_real(const double* src, const int32_t* map, int64_t d, double* dst,
                                int num_sms, cudaStream_t s);
 cudaError_t launch_observables(const double2* W, int64_t d, int ns, const double* O, int nobs,

@@ -353,17 +353,62 @@ __global__ void __launch_bounds__(TE_BLOCK) k_reorth_update(const double2* __res
 
 // w = sum_{k < m_eff} coef[k] u_k into column 0, then ||w|| for the next restart
 // (Algorithm 1 step 3; v_1 of the next Krylov space is w / ||w||).
+// With S (the sliced path: Re + Im of every column, S[k d + i]) the sum uses the
+// three-multiplication product of the SpMV: for c_k = a + ib and u = x + iy,
+// Re(c u) = a (x + y) - (a + b) y and Im(c u) = a (x + y) + (b - a) x, three DFMA
+// per element and column instead of four.
 __global__ void __launch_bounds__(TE_BLOCK) k_recombine(double2* __restrict__ V,
                                                         double* __restrict__ S, int64_t d,
                                                         DevState* st, double* partials) {
     __shared__ double sh[32];
     __shared__ double2 c[TE_M_MAX];
+    __shared__ double ca[TE_M_MAX], cp[TE_M_MAX], cq[TE_M_MAX];
     if (st->status != 0) return;
     const int nk = st->last_m_eff;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) c[k] = st->coef[k];
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const double2 ck = st->coef[k];
+        c[k] = ck;
+        ca[k] = ck.x;                // a
+        cp[k] = ck.y - ck.x;         // b - a
+        cq[k] = ck.x + ck.y;         // a + b
+    }
     __syncthreads();
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
+    if (S) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+            int k = 0;
+            for (; k + 4 <= nk; k += 4) {
+                double2 a[4];
+                double z[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = __ldcs(V + (size_t)(k + q) * d + i);
+                    z[q] = __ldcs(S + (size_t)(k + q) * d + i);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    k1 = fma(ca[k + q], z[q], k1);
+                    k2 = fma(cp[k + q], a[q].x, k2);
+                    k3 = fma(cq[k + q], a[q].y, k3);
+                }
+            }
+            for (; k < nk; ++k) {
+                const double2 a = __ldcs(V + (size_t)k * d + i);
+                const double z = __ldcs(S + (size_t)k * d + i);
+                k1 = fma(ca[k], z, k1);
+                k2 = fma(cp[k], a.x, k2);
+                k3 = fma(cq[k], a.y, k3);
+            }
+            const double re = k1 - k3, im = k1 + k2;
+            V[i] = make_double2(re, im);
+            S[i] = re + im;
+            acc = fma(re, re, acc);
+            acc = fma(im, im, acc);
+        }
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d && !S;
          i += (int64_t)gridDim.x * blockDim.x) {
         double re = 0.0, im = 0.0;
         int k = 0;
@@ -387,7 +432,6 @@ __global__ void __launch_bounds__(TE_BLOCK) k_recombine(double2* __restrict__ V,
             im = fma(c[k].y, a.x, im);
         }
         V[i] = make_double2(re, im);
-        if (S) S[i] = re + im;
         acc += re * re + im * im;
     }
     const double s = block_sum(acc, sh);

@@ -117,11 +117,15 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_sample_omega(DevState* st, 
 
 // ---------------------------------------------------------------- KS2
 
+// With S (Re + Im of every Krylov column, the sliced path) each product takes the
+// three-multiplication form of the recombination kernel, summed in the same order,
+// so the sample at the end of a step equals the state that step returns bit for bit.
 __global__ void __launch_bounds__(TE_BLOCK) k_sample_combine(const double2* __restrict__ V,
+                                                             const double* __restrict__ S,
                                                              int64_t d, DevState* st,
                                                              const double2* __restrict__ coef,
                                                              int mcap, double2* __restrict__ out) {
-    __shared__ double2 c[kGroup][TE_M_MAX];
+    __shared__ double ca[kGroup][TE_M_MAX], cp[kGroup][TE_M_MAX], cq[kGroup][TE_M_MAX];
     if (!st->active || st->status != 0) return;
     const int lo = st->samp_lo, hi = st->samp_hi;
     const int n = st->last_m_eff;
@@ -130,7 +134,15 @@ __global__ void __launch_bounds__(TE_BLOCK) k_sample_combine(const double2* __re
         __syncthreads();
         for (int i = threadIdx.x; i < ng * n; i += blockDim.x) {
             const int q = i / n, k = i - q * n;
-            c[q][k] = coef[(size_t)(g0 + q) * mcap + k];
+            const double2 c = coef[(size_t)(g0 + q) * mcap + k];
+            if (S) {
+                ca[q][k] = c.x;            // a
+                cp[q][k] = c.y - c.x;      // b - a
+                cq[q][k] = c.x + c.y;      // a + b
+            } else {
+                ca[q][k] = c.x;
+                cp[q][k] = c.y;
+            }
         }
         __syncthreads();
         for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d;
@@ -138,15 +150,40 @@ __global__ void __launch_bounds__(TE_BLOCK) k_sample_combine(const double2* __re
             double re[kGroup], im[kGroup];
 #pragma unroll
             for (int q = 0; q < kGroup; ++q) re[q] = im[q] = 0.0;
-            for (int k = 0; k < n; ++k) {
-                const double2 u = __ldg(V + (size_t)k * d + e);
+            if (S) {
+                double k3[kGroup];
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) k3[q] = 0.0;
+                // re carries sum a (x + y), im sum (b - a) x, k3 sum (a + b) y
+                for (int k = 0; k < n; ++k) {
+                    const double2 u = __ldg(V + (size_t)k * d + e);
+                    const double z = __ldg(S + (size_t)k * d + e);
+#pragma unroll
+                    for (int q = 0; q < kGroup; ++q) {
+                        if (q < ng) {
+                            re[q] = fma(ca[q][k], z, re[q]);
+                            im[q] = fma(cp[q][k], u.x, im[q]);
+                            k3[q] = fma(cq[q][k], u.y, k3[q]);
+                        }
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q) {
-                    if (q < ng) {
-                        re[q] = fma(c[q][k].x, u.x, re[q]);
-                        re[q] = fma(-c[q][k].y, u.y, re[q]);
-                        im[q] = fma(c[q][k].x, u.y, im[q]);
-                        im[q] = fma(c[q][k].y, u.x, im[q]);
+                    const double k1 = re[q];
+                    re[q] = k1 - k3[q];
+                    im[q] = k1 + im[q];
+                }
+            } else {
+                for (int k = 0; k < n; ++k) {
+                    const double2 u = __ldg(V + (size_t)k * d + e);
+#pragma unroll
+                    for (int q = 0; q < kGroup; ++q) {
+                        if (q < ng) {
+                            re[q] = fma(ca[q][k], u.x, re[q]);
+                            re[q] = fma(-cp[q][k], u.y, re[q]);
+                            im[q] = fma(ca[q][k], u.y, im[q]);
+                            im[q] = fma(cp[q][k], u.x, im[q]);
+                        }
                     }
                 }
             }
@@ -233,12 +270,12 @@ cudaError_t sample_prepare() {
 }
 
 cudaError_t launch_sample_kernels(DevState* st, const double* ts, int ns, int mcap, double2* coef,
-                                  double* bound, const double2* V, int64_t d, double2* out,
-                                  int grid_stream, cudaStream_t s) {
+                                  double* bound, const double2* V, const double* S, int64_t d,
+                                  double2* out, int grid_stream, cudaStream_t s) {
     const int g1 = ns < 32 ? (ns > 0 ? ns : 1) : 32;
     k_sample_omega<<<g1, TE_STEP_THREADS, sample_omega_smem(mcap), s>>>(st, ts, ns, mcap, coef,
                                                                       bound);
-    k_sample_combine<<<grid_stream, TE_BLOCK, 0, s>>>(V, d, st, coef, mcap, out);
+    k_sample_combine<<<grid_stream, TE_BLOCK, 0, s>>>(V, S, d, st, coef, mcap, out);
     k_sample_advance<<<1, 32, 0, s>>>(st);
     return cudaGetLastError();
 }
