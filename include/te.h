@@ -233,6 +233,18 @@ void te_matrix_free(te_matrix* H);
  * receives the fastest product time.  repeats: 1..100. */
 te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* best_ms);
 
+/* ---- measurement -------------------------------------------------------- */
+
+/* The FP64 fused multiply-add rate the context's GPU sustains, in TFLOP/s
+ * (2 FLOP per FMA), measured on independent FMA chains with no memory traffic:
+ * the attainable ceiling of the solve's FP64-bound products (the SpMV of
+ * Sec. 2.1, the orthogonalisation and the recombination of Algorithm 1).  Runs
+ * for about 0.1 s on the context's stream after the caller's queued work,
+ * allocates and frees a 1 MB scratch, and returns when the result is in
+ * *tflops (host pointer).  Errors: TE_ERR_INVALID_ARG (NULL argument),
+ * TE_ERR_CUDA. */
+te_status te_measure_fp64(te_ctx* ctx, double* tflops);
+
 /* ---- products and solves ------------------------------------------------ */
 
 /* y = H x (Sec. 2.1: the sparse product that dominates each Lanczos step).

@@ -53,6 +53,16 @@ constexpr int kTaskEntries = 1536;   // stored entries per SpMV task (slices are
 // The SpMV keeps per-group counters in its partials buffer, above what the other
 // reduction kernels of a restart write (they use at most kCtrMin entries from 0),
 // so they persist (at zero) from one launch to the next.
+// Tasks: the first sell_big_tasks() take tpt slices each, the remaining slices
+// (about the last eighth) go out one per task, which shortens the ragged end.
+__host__ __device__ __forceinline__ int64_t sell_big_tasks(int64_t nslices, int tpt) {
+    return tpt > 1 ? (nslices - nslices / 8) / tpt : 0;
+}
+__host__ __device__ __forceinline__ int64_t sell_ntasks(int64_t nslices, int tpt) {
+    const int64_t nb = sell_big_tasks(nslices, tpt);
+    return tpt > 1 ? nb + (nslices - nb * tpt) : nslices;
+}
+
 __host__ __device__ __forceinline__ int64_t sell_ctr_offset(int64_t ntasks) {
     const int64_t ngroups = (ntasks + kGroup - 1) / kGroup;
     return ntasks + ngroups > kCtrMin ? ntasks + ngroups : kCtrMin;
@@ -328,9 +338,10 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
 // hold Re x_i + Im x_i.
 //
 // Each warp takes one task (tpt consecutive slices, about kTaskEntries stored
-// entries) at a time from an atomic counter, asking for the next one only when
-// it is done with the current one (reserving ahead left every warp holding an
-// unstarted task at the end and stretched the tail).  SMs that run slower simply
+// entries; the last eighth of the slices one per task, so that the tasks still
+// running at the end are short) at a time from an atomic counter, asking for the
+// next one only when it is done with the current one (reserving ahead left every
+// warp holding an unstarted task at the end and stretched the tail).  SMs that run slower simply
 // take fewer tasks, and the kernel ends within about one task of perfect
 // balance.  Re<x, y> is summed without atomics on values: every task
 // stores its warp's partial; the warp that completes a group of kGroup tasks (a
@@ -353,7 +364,8 @@ __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* _
         if (j > 0) bp = st->beta[j - 1] * st->scale[j - 1];
     }
     const int lane = threadIdx.x & 31;
-    const int64_t ntasks = (nslices + tpt - 1) / tpt;
+    const int64_t ntasks = sell_ntasks(nslices, tpt);
+    const int64_t nbig = sell_big_tasks(nslices, tpt);
     const int64_t ngroups = (ntasks + kGroup - 1) / kGroup;
     double* gpart = partials + ntasks;
     unsigned int* gctr = reinterpret_cast<unsigned int*>(partials + sell_ctr_offset(ntasks));
@@ -362,8 +374,9 @@ __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* _
     if (lane == 0) c = atomicAdd(next, 1u);
     c = __shfl_sync(0xffffffffu, c, 0);
     while ((int64_t)c < ntasks) {
-        const int64_t s0 = (int64_t)c * tpt;
-        const int64_t s1 = s0 + tpt < nslices ? s0 + tpt : nslices;
+        const bool big = (int64_t)c < nbig;
+        const int64_t s0 = big ? (int64_t)c * tpt : nbig * tpt + ((int64_t)c - nbig);
+        const int64_t s1 = big ? s0 + tpt : s0 + 1;
         double acc = 0.0;
 #pragma unroll 1
         for (int64_t s = s0; s < s1; ++s) {
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sell(
     spmv_sell_body(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
 }
 
-__global__ void __launch_bounds__(TE_BLOCK, 5) k_spmv_sellv(
+__global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sellv(
     IndexedSlices M, const double2* __restrict__ x, const double* __restrict__ xs,
     const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
     int tpt, DevState* st, int j, int mode, double* partials) {
@@ -627,6 +640,6 @@ cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, dou
 // partials the SpMV needs: per-slice and per-group sums, then the group counters
 // (which must be zero before the first launch).
 int64_t sell_partials(const te_matrix* H) {
-    const int64_t ntasks = (H->nslices + H->sell_tpt - 1) / H->sell_tpt;
+    const int64_t ntasks = sell_ntasks(H->nslices, H->sell_tpt);
     return sell_ctr_offset(ntasks) + (ntasks + kGroup - 1) / kGroup;
 }

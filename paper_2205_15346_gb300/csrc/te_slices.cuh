@@ -26,22 +26,33 @@ struct FullSlices {
         const double2* qp = vpq + o + lane;
         const int32_t* cp = col + o + lane;
         double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        // four entries per trip, as in the value-indexed form below
         int k = 0;
 #pragma unroll 1
-        for (; k + 2 <= w; k += 2) {
-            const double a0 = __ldcs(ap + 32 * k), a1 = __ldcs(ap + 32 * (k + 1));
-            const double2 q0 = __ldcs(qp + 32 * k), q1 = __ldcs(qp + 32 * (k + 1));
-            const int c0 = __ldcs(cp + 32 * k), c1 = __ldcs(cp + 32 * (k + 1));
-            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
-            k1 = fma(a0, z0, k1);
-            k2 = fma(q0.x, x0.x, k2);
-            k3 = fma(q0.y, x0.y, k3);
-            k1 = fma(a1, z1, k1);
-            k2 = fma(q1.x, x1.x, k2);
-            k3 = fma(q1.y, x1.y, k3);
+        for (; k + 4 <= w; k += 4) {
+            int c[4];
+            double a[4], z[4];
+            double2 q[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldcs(cp + 32 * (k + u));
+                a[u] = __ldcs(ap + 32 * (k + u));
+                q[u] = __ldcs(qp + 32 * (k + u));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xv[u] = __ldg(x + c[u]);
+                z[u] = __ldg(xs + c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                k1 = fma(a[u], z[u], k1);
+                k2 = fma(q[u].x, xv[u].x, k2);
+                k3 = fma(q[u].y, xv[u].y, k3);
+            }
         }
-        if (k < w) {
+#pragma unroll 1
+        for (; k < w; ++k) {
             const double a0 = __ldcs(ap + 32 * k);
             const double2 q0 = __ldcs(qp + 32 * k);
             const int c0 = __ldcs(cp + 32 * k);
@@ -70,33 +81,34 @@ struct IndexedSlices {
         const uint16_t* ip = vidx + o + lane;
         const int32_t* cp = col + o + lane;
         double k1 = 0.0, k2 = 0.0, k3 = 0.0;
-        // columns and table indices are loaded one pair ahead of their gathers
-        int c0 = 0, c1 = 0, q0 = 0, q1 = 0;
-        if (w >= 2) {
-            c0 = __ldcs(cp); c1 = __ldcs(cp + 32);
-            q0 = __ldcs(ip); q1 = __ldcs(ip + 32);
-        }
+        // four entries per trip: sixteen gathers in flight per lane before the FMAs
         int k = 0;
 #pragma unroll 1
-        for (; k + 2 <= w; k += 2) {
-            int n0 = 0, n1 = 0, m0 = 0, m1 = 0;
-            if (k + 4 <= w) {
-                n0 = __ldcs(cp + 32 * (k + 2)); n1 = __ldcs(cp + 32 * (k + 3));
-                m0 = __ldcs(ip + 32 * (k + 2)); m1 = __ldcs(ip + 32 * (k + 3));
+        for (; k + 4 <= w; k += 4) {
+            int c[4], q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldcs(cp + 32 * (k + u));
+                q[u] = __ldcs(ip + 32 * (k + u));
             }
-            const double a0 = __ldg(ta + q0), a1 = __ldg(ta + q1);
-            const double2 p0 = __ldg(tpq + q0), p1 = __ldg(tpq + q1);
-            const double2 x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            const double z0 = __ldg(xs + c0), z1 = __ldg(xs + c1);
-            k1 = fma(a0, z0, k1);
-            k2 = fma(p0.x, x0.x, k2);
-            k3 = fma(p0.y, x0.y, k3);
-            k1 = fma(a1, z1, k1);
-            k2 = fma(p1.x, x1.x, k2);
-            k3 = fma(p1.y, x1.y, k3);
-            c0 = n0; c1 = n1; q0 = m0; q1 = m1;
+            double a[4], z[4];
+            double2 p[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __ldg(ta + q[u]);
+                p[u] = __ldg(tpq + q[u]);
+                xv[u] = __ldg(x + c[u]);
+                z[u] = __ldg(xs + c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                k1 = fma(a[u], z[u], k1);
+                k2 = fma(p[u].x, xv[u].x, k2);
+                k3 = fma(p[u].y, xv[u].y, k3);
+            }
         }
-        if (k < w) {
+#pragma unroll 1
+        for (; k < w; ++k) {
             const int qq = __ldcs(ip + 32 * k);
             const int cc = __ldcs(cp + 32 * k);
             const double a0 = __ldg(ta + qq);

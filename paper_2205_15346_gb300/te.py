@@ -107,6 +107,7 @@ _SIGS = {
     "te_matrix_export": (C.c_int32, [_P, _P, _P, _P, _P, C.c_uint32]),
     "te_matrix_free": (None, [_P]),
     "te_matrix_tune": (C.c_int32, [_P, _P, C.c_int32, C.POINTER(C.c_double)]),
+    "te_measure_fp64": (C.c_int32, [_P, C.POINTER(C.c_double)]),
     "te_spmv": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_spmv_noalloc": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
@@ -335,6 +336,13 @@ def te_matrix_tune(ctx, H, repeats: int = 5) -> float:
     best = C.c_double()
     _check(ctx, lib().te_matrix_tune(ctx, H, int(repeats), C.byref(best)))
     return best.value
+
+
+def te_measure_fp64(ctx) -> float:
+    """The FP64 FMA rate this GPU sustains on independent chains (TFLOP/s)."""
+    r = C.c_double()
+    _check(ctx, lib().te_measure_fp64(ctx, C.byref(r)))
+    return r.value
 
 
 def te_matrix_free(H) -> None:

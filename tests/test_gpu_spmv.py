@@ -150,3 +150,21 @@ def test_autotune_keeps_the_product_and_solves_exact(te, ctx):
         assert np.linalg.norm(out - krylov.evolve(A, v0, 2.0, 1e-9, 20).v) <= 2e-9 + 1e-12
     finally:
         te.te_matrix_free(H)
+
+
+def test_measure_fp64_rate_is_within_the_pipe_peak(te, ctx):
+    """te_measure_fp64 executes its FMA chains: the rate is a sizeable fraction of
+    the FP64 pipe's derived peak (SMs x 2 FMA lanes x 2 FLOP x maximum SM clock)
+    and does not exceed it."""
+    import subprocess
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", "0"], capture_output=True, text=True, timeout=30).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pytest.skip("nvidia-smi did not report the maximum SM clock")
+    peak = sms * 2 * 2 * mhz * 1e6 / 1e12
+    r = te.te_measure_fp64(ctx)
+    assert 0.3 * peak < r <= 1.02 * peak, (r, peak)
