@@ -38,6 +38,9 @@ import workloads as W  # noqa: E402
 METRIC = "exp(-iHt)v solves/s and p50/p99 latency at bound 1e-8; SpMV HBM GB/s vs peak"
 WORKLOAD = "xxzdm_L22"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_spmv_sellv_xxzdm_L22.md")
+# committed ncu summaries of the dominant kernel (K1) per single-solve workload
+K1_SUMMARIES = {"xxzdm_L22": PROFILE_SUMMARY,
+                "memory_K10": os.path.join(ROOT, "profiles", "k_spmv_sellr_memory_K10.md")}
 K1_SOURCES = [os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", f)
               for f in ("te_sell.cu", "te_slices.cuh")]
 # FP64 issue rate of GB300: 2 DFMA lanes per SM per cycle (ncu reports a sustained
@@ -397,7 +400,14 @@ def run_ours(args):
     # u_{j-1} read and y written per row; slice offsets.  HBM is reported beside it.
     nnz = info["nnz"]
     nslices = (d + 31) // 32
-    if info["sell_dict"] > 0:
+    if info["sell_dict"] > 0 and info["sell_real"]:
+        # real value table: 2 DFMA (4 FLOP) per off-diagonal entry, no x+y gather and
+        # no combination of three sums per row
+        off = nnz - d
+        k1_bytes = 6 * off + 8 * d + 4 * (nslices + 1) + 48 * d + 8 * info["sell_dict"]
+        k1_flops = 4 * off + 14 * d
+        k1_flops_complex = 8 * off + 16 * d
+    elif info["sell_dict"] > 0:
         # value-indexed copy: column + 16-bit table index per off-diagonal entry, the
         # real diagonal per row (the model builders store every diagonal entry, so
         # there are nnz - d off-diagonal entries); diagonal term 2 DFMA per row
@@ -436,8 +446,10 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
-                         "traffic": recorded_traffic(),
-                         "kernel": (("k_spmv_sellv" if info["sell_dict"] > 0 else "k_spmv_sell") +
+                         "traffic": (recorded_traffic(K1_SUMMARIES[args.workload])
+                                     if args.workload in K1_SUMMARIES else None),
+                         "kernel": (("k_spmv_sellr" if info["sell_dict"] > 0 and info["sell_real"]
+                                     else "k_spmv_sellv" if info["sell_dict"] > 0 else "k_spmv_sell") +
                                     " (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)"),
                          "timing": ("CUDA events around the Lanczos step m/2 product of every "
                                     "restart inside the timed solves"),
@@ -692,6 +704,8 @@ def run_multi(args):
     # roofline of the grouped SpMV (KM1): executed FP64 work over all its launches
     def flops_per_matvec(info):
         d, nnz = info["d"], info["nnz"]
+        if info["sell_dict"] > 0 and info["sell_real"]:
+            return 4 * (nnz - d) + 14 * d
         if info["sell_dict"] > 0:
             return 6 * (nnz - d) + 16 * d
         return 6 * nnz + 12 * d

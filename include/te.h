@@ -134,6 +134,9 @@ typedef struct te_matrix_info {
                                   16-bit table index per entry, real diagonal apart); 0 when the
                                   copy stores full values (complex diagonal or > 65535 values) */
     int32_t sell_tpt;          /* slices (of 32 rows) per work item of the sliced SpMV */
+    int32_t sell_real;         /* 1 when the value table is real (every off-diagonal value has a
+                                  zero imaginary part): the product then takes 2 DFMA per entry
+                                  instead of 3 */
 } te_matrix_info;
 
 /* Synthetic model Hamiltonians built on the device (Sec. 3: the matrix of an
@@ -258,11 +261,12 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y,
 
 /* y = H x and Re <x, H x>, like te_spmv, but without allocating anything.
  * The paper has no counterpart: this exists for callers that cannot allocate
- * device memory at the moment they need the product -- code running inside a
- * CUDA stream capture (cudaMalloc is illegal there), code whose framework owns
- * all device memory through its own pool, and latency-critical loops that
- * cannot afford cudaMalloc or the device-wide synchronisation implied by
- * cudaFree.  te_spmv, by contrast, allocates staging buffers for host vectors.
+ * device memory at the moment they need the product -- code whose framework
+ * owns all device memory through its own pool (a stray cudaMalloc can fail or
+ * fragment it), services that must keep their device footprint fixed once
+ * started, and latency-critical loops that cannot afford cudaMalloc or the
+ * device-wide synchronisation implied by cudaFree.  te_spmv, by contrast,
+ * allocates staging buffers for host vectors.
  *   x, y: device pointers (flags must contain TE_PTR_DEVICE), distinct,
  *         complex128, length d; x_dot_y: host pointer or NULL.
  *   d must not exceed TE_NOALLOC_MAX_D (else TE_ERR_UNSUPPORTED, nothing runs).

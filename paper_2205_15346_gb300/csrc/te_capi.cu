@@ -704,6 +704,7 @@ te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
     info->sell_nnz = H->sell_nnz;
     info->sell_dict = H->dict_n;
     info->sell_tpt = H->sell_tpt;
+    info->sell_real = H->dict_real ? 1 : 0;
     return TE_OK;
 }
 

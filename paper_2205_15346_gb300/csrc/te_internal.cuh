@@ -112,6 +112,7 @@ struct te_matrix {
     double* dict_a = nullptr;        // value table (index 0 = 0): Re h
     double2* dict_pq = nullptr;      // value table: (Im h - Re h, Re h + Im h)
     int32_t dict_n = 0;              // distinct off-diagonal values (0: full-value form)
+    bool dict_real = false;          // every off-diagonal value is real (2-DFMA product)
     int64_t nslices = 0;
     int64_t sell_nnz = 0;        // stored entries including padding
     int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)
@@ -225,7 +226,7 @@ cudaError_t step_prepare();
 
 // SELL form (te_sell.cu)
 te_status build_sell(te_ctx* ctx, te_matrix* H);
-int sell_grid(int64_t nslices, int num_sms, bool indexed);
+int sell_grid(int64_t nslices, int num_sms, int form);   // 0 full, 1 indexed, 2 real indexed
 int64_t sell_partials(const te_matrix* H);
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,

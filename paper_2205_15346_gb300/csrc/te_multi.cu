@@ -33,6 +33,7 @@
 
 using te_slices::FullSlices;
 using te_slices::IndexedSlices;
+using te_slices::RealIndexedSlices;
 
 struct MProb {
     const int32_t* off;
@@ -47,7 +48,7 @@ struct MProb {
     int64_t nslices;
     int64_t elem0;             // element offset in every concatenated block
     int32_t tpt;               // slices per SpMV task
-    int32_t pad;
+    int32_t real;              // value-indexed form with a real table (2-DFMA product)
 };
 
 namespace {
@@ -157,7 +158,10 @@ __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_multi(
         const double2* xprev = Xp ? Xp + P.elem0 : nullptr;
         double2* y = Y + P.elem0;
         double acc;
-        if (P.vidx) {
+        if (P.vidx && P.real) {
+            const RealIndexedSlices M{P.off, P.col, P.vidx, P.ta, P.diag};
+            acc = run_task(M, s0, s1, lane, P.d, x, xs, xprev, y, cx, bp);
+        } else if (P.vidx) {
             const IndexedSlices M{P.off, P.col, P.vidx, P.ta, P.tpq, P.diag};
             acc = run_task(M, s0, s1, lane, P.d, x, xs, xprev, y, cx, bp);
         } else {
@@ -456,6 +460,7 @@ te_status create_multi_plan(te_ctx* ctx, int n, const te_matrix* const* H, int m
         q.d = A->d;
         q.nslices = A->nslices;
         q.tpt = A->sell_tpt;
+        q.real = A->dict_real ? 1 : 0;
         q.elem0 = off;
         p->elem0.push_back(off);
         // keep every problem's segment 16-byte aligned and a whole number of slices

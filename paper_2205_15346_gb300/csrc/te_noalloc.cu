@@ -1,10 +1,11 @@
 // te_noalloc.cu -- te_spmv_noalloc: y = H x and Re <x, H x> without any allocation.
 //
 // Some callers cannot allocate device memory when they need a product: code
-// running inside a CUDA stream capture (where cudaMalloc is not allowed), code
-// that lives under a framework owning all device memory through its own pool,
-// and latency-critical loops that must not pay for cudaMalloc or the implicit
-// device-wide synchronisation of cudaFree.  For them this file offers a
+// that lives under a framework owning all device memory through its own pool
+// (a stray cudaMalloc there can fail or fragment the pool), services that must
+// keep their device footprint fixed once started, and latency-critical loops
+// that must not pay for cudaMalloc or the implicit device-wide synchronisation
+// of cudaFree.  For them this file offers a
 // variant of the library's SpMV-with-energy kernel whose reduction scratch (one
 // partial sum per thread block, an arrival counter and the result slot) lives
 // in a fixed, file-scope device array instead of memory allocated per call.

@@ -33,7 +33,8 @@
 // 6 bytes per entry instead of 28, which leaves the product bound by FP64 issue
 // alone.  The table is found on the device with a hash set keyed on the value's
 // 128 bits; a matrix with a complex diagonal or more than 65535 distinct
-// off-diagonal values keeps the full-value form.
+// off-diagonal values keeps the full-value form.  When every off-diagonal
+// value is real, the product uses the table's a alone: two DFMA per entry.
 #include <algorithm>
 #include <vector>
 
@@ -42,6 +43,7 @@
 
 using te_slices::FullSlices;
 using te_slices::IndexedSlices;
+using te_slices::RealIndexedSlices;
 
 namespace {
 
@@ -167,7 +169,8 @@ __device__ __forceinline__ VKey read_slot(const VKey* slot) {
 }
 
 // flags[0]: table full or probe limit hit; flags[1]: complex diagonal entry;
-// flags[2]: distinct values inserted.  A value may land in two slots when two
+// flags[2]: distinct values inserted; flags[3]: an off-diagonal value with a
+// nonzero imaginary part (the table is complex).  A value may land in two slots when two
 // threads race on it (harmless: both hold the same value).
 __global__ void k_dict_insert(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                               const double2* __restrict__ val, int64_t d, VKey* slots, int* flags) {
@@ -179,6 +182,7 @@ __global__ void k_dict_insert(const int32_t* __restrict__ rowptr, const int32_t*
                 if (v.y != 0.0) atomicExch(&flags[1], 1);
                 continue;
             }
+            if (v.y != 0.0) atomicExch(&flags[3], 1);
             const VKey key = vkey(v);
             unsigned int h = vhash(key);
             bool placed = false;
@@ -461,6 +465,13 @@ __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sellv(
     spmv_sell_body(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
 }
 
+__global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sellr(
+    RealIndexedSlices M, const double2* __restrict__ x, const double* __restrict__ xs,
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    int tpt, DevState* st, int j, int mode, double* partials) {
+    spmv_sell_body(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
+}
+
 // dst[i] = src[map[i]]  (map = perm: old -> new order; map = iperm: back);
 // with dsum, also dsum[i] = Re dst[i] + Im dst[i] for the product's 3M form.
 __global__ void k_gather(const double2* __restrict__ src, const int32_t* __restrict__ map,
@@ -507,6 +518,7 @@ te_status build_dict(te_ctx* ctx, te_matrix* H, VKey** slots_out, uint16_t** slo
     k_dict_compact<<<1, 1024, 0, s>>>(slots, slot_idx, H->dict_a, H->dict_pq);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     H->dict_n = hf[2];
+    H->dict_real = hf[3] == 0;
     *ok = true;
     return TE_OK;
 }
@@ -539,6 +551,7 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
         H->dict_a = nullptr;
         H->dict_pq = nullptr;
         H->dict_n = 0;
+        H->dict_real = false;
     }
     cudaError_t e = cudaMalloc(&H->perm, sizeof(int32_t) * (size_t)nslices * 32);
     if (e == cudaSuccess) e = cudaMalloc(&H->iperm, sizeof(int32_t) * (size_t)d);
@@ -597,13 +610,14 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
     cleanup();
     if (e != cudaSuccess) return cuda_error(ctx, e, "filling the sliced copy");
     if (dict && hf[0]) return set_error(ctx, TE_ERR_INTERNAL, "value table lookup failed");
-    H->sell_grid = sell_grid(nslices, ctx->num_sms, dict);
+    H->sell_grid = sell_grid(nslices, ctx->num_sms, dict ? (H->dict_real ? 2 : 1) : 0);
     return TE_OK;
 }
 
-int sell_grid(int64_t nslices, int num_sms, bool indexed) {
+int sell_grid(int64_t nslices, int num_sms, int form) {
     int nb = 0;
-    if (indexed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv, TE_BLOCK, 0);
+    if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellr, TE_BLOCK, 0);
+    else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv, TE_BLOCK, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sell, TE_BLOCK, 0);
     if (nb < 1) nb = 1;
     const int64_t need = (nslices + (TE_BLOCK / 32) - 1) / (TE_BLOCK / 32);
@@ -616,7 +630,11 @@ int sell_grid(int64_t nslices, int num_sms, bool indexed) {
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,
                              double* partials, cudaStream_t s) {
-    if (H->sell_idx) {
+    if (H->sell_idx && H->dict_real) {
+        const RealIndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->sell_diag};
+        k_spmv_sellr<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+                                                      H->sell_tpt, st, j, mode, partials);
+    } else if (H->sell_idx) {
         const IndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->dict_pq,
                               H->sell_diag};
         k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,

@@ -124,4 +124,58 @@ struct IndexedSlices {
     }
 };
 
+// Value-indexed form of a matrix whose off-diagonal values are all real (b = 0,
+// e.g. the transverse-field Ising chain): Re(h x) = a x and Im(h x) = a y, two
+// DFMA per entry instead of three, and no gather of x + y.  The table is the
+// same a column of the complex form.
+struct RealIndexedSlices {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ col;
+    const uint16_t* __restrict__ vidx;
+    const double* __restrict__ ta;
+    const double* __restrict__ diag;
+    __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
+                                           const double* __restrict__ /*xs*/, int64_t r,
+                                           double2 xr) const {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const uint16_t* ip = vidx + o + lane;
+        const int32_t* cp = col + o + lane;
+        double k1 = 0.0, k2 = 0.0;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 4 <= w; k += 4) {
+            int c[4], q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldcs(cp + 32 * (k + u));
+                q[u] = __ldcs(ip + 32 * (k + u));
+            }
+            double a[4];
+            double2 xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __ldg(ta + q[u]);
+                xv[u] = __ldg(x + c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                k1 = fma(a[u], xv[u].x, k1);
+                k2 = fma(a[u], xv[u].y, k2);
+            }
+        }
+#pragma unroll 1
+        for (; k < w; ++k) {
+            const int qq = __ldcs(ip + 32 * k);
+            const int cc = __ldcs(cp + 32 * k);
+            const double a0 = __ldg(ta + qq);
+            const double2 x0 = __ldg(x + cc);
+            k1 = fma(a0, x0.x, k1);
+            k2 = fma(a0, x0.y, k2);
+        }
+        const double dg = r >= 0 ? __ldcs(diag + r) : 0.0;
+        return make_double2(fma(dg, xr.x, k1), fma(dg, xr.y, k2));
+    }
+};
+
 }  // namespace te_slices

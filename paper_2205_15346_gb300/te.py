@@ -75,7 +75,8 @@ class te_stats(C.Structure):
 class te_matrix_info(C.Structure):
     _fields_ = [("d", C.c_int64), ("nnz", C.c_int64), ("norm1", C.c_double),
                 ("max_row_nnz", C.c_int32), ("spmv_lanes", C.c_int32), ("sell_nnz", C.c_int64),
-                ("sell_dict", C.c_int32), ("sell_tpt", C.c_int32)]
+                ("sell_dict", C.c_int32), ("sell_tpt", C.c_int32),
+                ("sell_real", C.c_int32)]
 
 
 class te_model_desc(C.Structure):

@@ -76,14 +76,17 @@ def test_spmv_single_row(te, ctx):
         te.te_matrix_free(H)
 
 
-@pytest.mark.parametrize("nvals,complex_diag,expect_table", [
-    (100, False, True),      # few distinct values, real diagonal: value-indexed copy
-    (None, False, False),    # every value distinct (> 65535): full-value copy
-    (100, True, False),      # complex diagonal: full-value copy
+@pytest.mark.parametrize("nvals,complex_diag,expect_table,real_table", [
+    (100, False, True, False),   # few distinct values, real diagonal: value-indexed copy
+    (100, False, True, True),    # the same with real values: the two-DFMA product
+    (None, False, False, False), # every value distinct (> 65535): full-value copy
+    (100, True, False, False),   # complex diagonal: full-value copy
+    (100, True, False, True),    # real off-diagonal values, complex diagonal: full-value copy
 ])
-def test_spmv_value_table_forms(te, ctx, nvals, complex_diag, expect_table):
+def test_spmv_value_table_forms(te, ctx, nvals, complex_diag, expect_table, real_table):
     """The sliced copy stores a 16-bit index into a table of distinct
-    off-diagonal values when it can; both forms give the oracle's product."""
+    off-diagonal values when it can (with a product of two DFMA per entry when
+    every one of them is real); all forms give the oracle's product."""
     d, per = 5000, 20
     offs = 1 + (W.uniform(201, per) * (d - 1)).astype(np.int64)
     offs = np.unique(offs)
@@ -95,7 +98,7 @@ def test_spmv_value_table_forms(te, ctx, nvals, complex_diag, expect_table):
         vals = (u[:n] - 0.5) + 1j * (u[n:] - 0.5)
     else:
         u = W.uniform(203, 2 * nvals)
-        table = (u[:nvals] - 0.5) + 1j * (u[nvals:] - 0.5)
+        table = (u[:nvals] - 0.5) + (0.0 if real_table else 1j * (u[nvals:] - 0.5))
         pick = (W.uniform(204, n) * nvals).astype(np.int64)
         vals = table[pick]
     dg = W.uniform(205, 2 * d) - 0.5
@@ -112,8 +115,9 @@ def test_spmv_value_table_forms(te, ctx, nvals, complex_diag, expect_table):
             mask = off.row != off.col
             distinct = len(np.unique(np.stack([off.data[mask].real, off.data[mask].imag], 1), axis=0))
             assert 0 < info["sell_dict"] <= distinct + 64     # racing inserts may repeat a value
+            assert info["sell_real"] == int(real_table)
         else:
-            assert info["sell_dict"] == 0
+            assert info["sell_dict"] == 0 and info["sell_real"] == 0
         check_spmv(te, ctx, H, A, 14)
         check_spmv(te, ctx, H, A, 15, torch_dev=True)
     finally:
@@ -124,10 +128,13 @@ def test_spmv_value_table_forms(te, ctx, nvals, complex_diag, expect_table):
     W.tfim_params(10, 1), W.xxzdm_params(12, 2), W.bose_params(8, 5, 4), W.memory_params(),
 ], ids=lambda p: p["model"])
 def test_model_matrices_use_value_table(te, ctx, params):
-    """The built-in models have real diagonals and few distinct couplings."""
+    """The built-in models have real diagonals and few distinct couplings; the
+    Ising chain and the paper's example system have real ones."""
     H = te.te_build_model(ctx, params)
     try:
-        assert te.te_matrix_info_get(H)["sell_dict"] > 0
+        info = te.te_matrix_info_get(H)
+        assert info["sell_dict"] > 0
+        assert info["sell_real"] == int(params["model"] in ("tfim", "memory"))
     finally:
         te.te_matrix_free(H)
 

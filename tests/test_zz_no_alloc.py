@@ -1,8 +1,9 @@
 """te_spmv_noalloc, the allocation-free SpMV entry point, against te_spmv.
 
 It serves callers that cannot allocate device memory when they need a product
-(inside a stream capture, under a framework that owns all device memory, or in
-loops that cannot pay for cudaMalloc/cudaFree).  Its scratch is a fixed device
+(under a framework that owns all device memory through its own pool, in a
+service whose device footprint is fixed once started, or in loops that cannot
+pay for cudaMalloc/cudaFree).  Its scratch is a fixed device
 array shared by all calls, so the test calls it twice in a row, on different
 inputs and then on the same input again, and compares each result with the
 allocating te_spmv on the same inputs.  This file is collected last on purpose.
