@@ -71,9 +71,14 @@ typedef int32_t te_status;
 /* te_options.small_exp: how exp(-i H_m tau) e_1 and the error integrand are evaluated */
 #define TE_SMALLEXP_CHEB 0         /* Chebyshev/Bessel (Jacobi-Anger) series of the tridiagonal H_m (default) */
 #define TE_SMALLEXP_EIG  1         /* diagonalisation of H_m, the paper's choice (Sec. 2.4) */
+/* te_options.fused_lanczos */
+#define TE_FUSED_AUTO 0            /* small matrices (d <= 1024 x SMs, 155,648 on GB300) run the m
+                                      Lanczos steps of a restart as one cooperative kernel (default) */
+#define TE_FUSED_OFF  1            /* always one launch per product and per orthogonalisation */
 /* te_options.flags */
 #define TE_OPT_PROFILE 0x10u       /* time the fused SpMV of Lanczos step m/2 of every restart with
-                                      CUDA events (te_stats.spmv_*; one event pair per restart) */
+                                      CUDA events (te_stats.spmv_*; one event pair per restart; with
+                                      a fused Lanczos loop the pair brackets that whole kernel) */
 
 /*
  * Solver options.  te_default_options fills the defaults, which follow the
@@ -96,7 +101,10 @@ typedef struct te_options {
     int32_t  spmv_lanes;       /* 0: sliced-ELLPACK SpMV, one lane per row (default);
                                   1..32 (power of 2): CSR SpMV with that many lanes per row */
     int32_t  small_exp;        /* TE_SMALLEXP_CHEB (default) or TE_SMALLEXP_EIG */
-    int32_t  reserved;
+    int32_t  fused_lanczos;    /* TE_FUSED_AUTO (default) or TE_FUSED_OFF.  The fused loop applies
+                                  to the sliced SpMV (spmv_lanes 0) without reorthogonalisation;
+                                  it computes the same steps, summing alpha and beta in another
+                                  order */
 } te_options;
 
 /* Per-solve report.  err_bound is the sum of the accepted step errors (the
@@ -121,6 +129,7 @@ typedef struct te_stats {
     int64_t  quad_nodes;       /* integrand evaluations in those integrals */
     double   eig_mcycles;      /* 1e6 SM cycles spent diagonalising H_m (all restarts) */
     double   search_mcycles;   /* 1e6 SM cycles spent in the step search and omega */
+    int64_t  fused_restarts;   /* restarts whose Lanczos loop ran as one cooperative kernel */
 } te_stats;
 
 typedef struct te_matrix_info {
@@ -247,6 +256,20 @@ te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* bes
  * *tflops (host pointer).  Errors: TE_ERR_INVALID_ARG (NULL argument),
  * TE_ERR_CUDA. */
 te_status te_measure_fp64(te_ctx* ctx, double* tflops);
+
+/* The grid barrier of the fused Lanczos loop (te_options.fused_lanczos), run
+ * once over a cooperative grid of one 32-thread block per SM.  The paper has no
+ * counterpart: this exists so that tests can see that the barrier's bounded
+ * wait ends a wait that cannot complete with an error instead of a hang.
+ * absent_block < 0: every block arrives; the call returns TE_OK with *passed =
+ * the number of blocks.  absent_block = b (0 <= b < SMs): block b leaves without
+ * arriving; the others give up after about one second, *passed = 0 and the call
+ * returns TE_ERR_TIMEOUT, the status a solve reports when this happens inside
+ * its fused loop.  *ms (host pointer or NULL) receives the kernel's time.  Runs
+ * on the context's stream after the caller's queued work; allocates and frees
+ * 16 bytes.  Errors: TE_ERR_INVALID_ARG, TE_ERR_UNSUPPORTED (no cooperative
+ * launches), TE_ERR_CUDA. */
+te_status te_fused_barrier_check(te_ctx* ctx, int32_t absent_block, int32_t* passed, double* ms);
 
 /* ---- products and solves ------------------------------------------------ */
 

@@ -69,6 +69,7 @@ void free_plan(Plan* p) {
     if (p->st) cudaFree(p->st);
     if (p->partials) cudaFree(p->partials);
     if (p->partials_r) cudaFree(p->partials_r);
+    if (p->bar) cudaFree(p->bar);
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->st_init) cudaFreeHost(p->st_init);
     for (void* q : {(void*)p->samp_ts, (void*)p->samp_coef, (void*)p->samp_buf, (void*)p->samp_bound})
@@ -91,7 +92,16 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
     const int m = p->m;
     TE_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+    if (p->fused) {
+        // the m Lanczos steps as one cooperative kernel (small d), timed as a whole
+        if (p->profile) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
+        if (e == cudaSuccess)
+            e = launch_lanczos_fused(H, p->V, p->S, p->st, m, p->partials, p->bar, p->fused_grid,
+                                     p->fused_threads, s);
+        if (p->profile && e == cudaSuccess)
+            e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
+    }
+    for (int j = 0; j < m && e == cudaSuccess && !p->fused; ++j) {
         const double2* x = p->V + (size_t)j * d;
         const double2* xprev = j > 0 ? p->V + (size_t)(j - 1) * d : nullptr;
         double2* y = p->V + (size_t)(j + 1) * d;
@@ -141,9 +151,14 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
 }
 
 te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
-                      cudaStream_t s, Plan** out, int ns = 0) {
+                      int fused, cudaStream_t s, Plan** out, int ns = 0) {
     Plan* p = new Plan();
     p->H = H;
+    p->fused = fused;
+    if (fused && !fused_shape(H, ctx->num_sms, &p->fused_grid, &p->fused_threads)) {
+        delete p;
+        return set_error(ctx, TE_ERR_INTERNAL, "fused Lanczos loop requested for a matrix it does not fit");
+    }
     p->ns = ns;
     p->matrix_id = H->id;
     p->m = m;
@@ -155,7 +170,8 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
     const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
     p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
     p->grid_reorth = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 2);
-    const int max_grid = (int)std::max<int64_t>(std::max(p->grid_k1, p->grid_stream),
+    const int max_grid = (int)std::max<int64_t>(std::max(std::max(p->grid_k1, p->grid_stream),
+                                                         2 * p->fused_grid),
                                                 lanes ? 0 : sell_partials(H));
     p->bytes = plan_bytes(H->d, m, reorth, max_grid);
     cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
@@ -166,6 +182,7 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
     if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * (size_t)max_grid);
     if (e == cudaSuccess && reorth)
         e = cudaMalloc(&p->partials_r, sizeof(double) * (size_t)p->grid_reorth * TE_M_MAX * 2);
+    if (e == cudaSuccess && fused) e = cudaMalloc(&p->bar, 4 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState));
     if (e == cudaSuccess && ns > 0) {
@@ -203,19 +220,19 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
 // Take a cached idle plan that fits, or build one (dropping idle plans if the
 // device runs out of memory).
 te_status acquire_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
-                       cudaStream_t s, Plan** out) {
+                       int fused, cudaStream_t s, Plan** out) {
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         for (Plan* p : ctx->plans)
             if (!p->in_use && p->matrix_id == H->id && p->m == m && p->reorth == reorth &&
-                p->profile == profile && p->lanes == lanes) {
+                p->profile == profile && p->lanes == lanes && p->fused == fused) {
                 p->in_use = true;
                 *out = p;
                 return TE_OK;
             }
     }
     Plan* p = nullptr;
-    te_status st = create_plan(ctx, H, m, reorth, profile, lanes, s, &p);
+    te_status st = create_plan(ctx, H, m, reorth, profile, lanes, fused, s, &p);
     if (st == TE_ERR_OOM) {
         std::vector<Plan*> idle;
         {
@@ -227,7 +244,7 @@ te_status acquire_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int p
         }
         cudaStreamSynchronize(s);
         for (Plan* q : idle) free_plan(q);
-        st = create_plan(ctx, H, m, reorth, profile, lanes, s, &p);
+        st = create_plan(ctx, H, m, reorth, profile, lanes, fused, s, &p);
     }
     if (st) return st;
     p->in_use = true;
@@ -235,6 +252,15 @@ te_status acquire_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int p
     ctx->plans.push_back(p);
     *out = p;
     return TE_OK;
+}
+
+// Whether a solve with these options runs its Lanczos loops fused (te_fused.cu):
+// small d, the sliced SpMV, no reorthogonalisation, a device with cooperative
+// launches.
+int want_fused(const te_ctx* ctx, const te_matrix* H, const te_options& o) {
+    int g = 0, t = 0;
+    return (o.fused_lanczos == TE_FUSED_AUTO && o.spmv_lanes == 0 && o.reorth == TE_REORTH_NONE &&
+            ctx->coop && fused_shape(H, ctx->num_sms, &g, &t)) ? 1 : 0;
 }
 
 void release_plan(te_ctx* ctx, Plan* p) {
@@ -262,6 +288,8 @@ te_status check_solve_args(te_ctx* ctx, const te_matrix* H, double t, double tol
     if (!(o.t_step0 > 0.0) || !(o.shrink > 0.0 && o.shrink <= 1.0) || !(o.quad_rel_tol > 0.0) ||
         o.quad_max_levels < 3 || o.quad_max_levels > 20 || !(o.min_step_rel > 0.0))
         return set_error(ctx, TE_ERR_INVALID_ARG, "step or quadrature option out of range");
+    if (o.fused_lanczos != TE_FUSED_AUTO && o.fused_lanczos != TE_FUSED_OFF)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "fused_lanczos must be TE_FUSED_AUTO or TE_FUSED_OFF");
     if (o.spmv_lanes != 0 && (o.spmv_lanes < 1 || o.spmv_lanes > 32 ||
                               (o.spmv_lanes & (o.spmv_lanes - 1)) != 0))
         return set_error(ctx, TE_ERR_INVALID_ARG, "spmv_lanes must be 0 or a power of 2 <= 32");
@@ -332,7 +360,7 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
             }
             TE_CUDA_TRY(ctx, cudaGraphLaunch(p->exec, s));
             TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-            if (p->profile && p->m / 2 < h->last_m_eff) {   // the timed product ran
+            if (p->profile && (p->fused || p->m / 2 < h->last_m_eff)) {   // the timed work ran
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) {
                     S.spmv_ms += ms;
@@ -345,6 +373,8 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
                 result = h->status;
                 set_error(ctx, result, result == TE_ERR_STEP_UNDERFLOW
                                            ? "step size underflow: no step meets the error rate"
+                                       : result == TE_ERR_TIMEOUT
+                                           ? "a grid barrier of the fused Lanczos loop gave up waiting"
                                            : "solver failed on the device");
                 break;
             }
@@ -370,6 +400,7 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     S.quad_nodes = h->quad_nodes;
     S.eig_mcycles = 1e-6 * (double)h->eig_cycles;
     S.search_mcycles = 1e-6 * (double)h->search_cycles;
+    S.fused_restarts = p->fused ? h->restarts : 0;
     S.err_bound = h->err_acc;
     S.t_reached = (t >= 0.0 ? 1.0 : -1.0) * h->t_now;
     if (h->breakdowns) S.flags |= TE_FLAG_BREAKDOWN;
@@ -478,6 +509,7 @@ te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
     te_ctx* c = new te_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, device);
     // Work runs on the context's own non-blocking stream (CUDA graphs cannot be
     // captured on the legacy default stream); every call first waits for the
     // caller's stream and returns only after its own work has finished.
@@ -877,7 +909,8 @@ te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
     const int mu = (int)std::min<int64_t>(m, H->d);
     const int lanes = o.spmv_lanes;          // 0: SELL (default), > 0: CSR with that many lanes
     Plan* p = nullptr;
-    s = acquire_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, lanes, ctx->stream, &p);
+    s = acquire_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, lanes,
+                     want_fused(ctx, H, o), ctx->stream, &p);
     if (s) return s;
     s = run_solve(ctx, H, p, ctx->stream, v_in, t, tol, o, v_out, (o.flags & TE_PTR_DEVICE) != 0,
                   st, nullptr);
@@ -918,7 +951,8 @@ te_status te_evolve_sampled(te_ctx* ctx, const te_matrix* H, const double* v_in,
     const int mu = (int)std::min<int64_t>(m, d);
     const bool dev = (o.flags & TE_PTR_DEVICE) != 0;
     Plan* p = nullptr;
-    rs = create_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, 0, s, &p, n_samples);
+    rs = create_plan(ctx, H, mu, o.reorth, (o.flags & TE_OPT_PROFILE) ? 1 : 0, 0,
+                     want_fused(ctx, H, o), s, &p, n_samples);
     if (rs) return rs;
     auto done = [&](te_status r) {
         cudaStreamSynchronize(s);
@@ -1205,7 +1239,8 @@ void worker_loop(te_ctx* ctx) {
             Plan* p = nullptr;
             const int lanes = r->opt.spmv_lanes;
             res = acquire_plan(ctx, r->H, r->m, r->opt.reorth,
-                               (r->opt.flags & TE_OPT_PROFILE) ? 1 : 0, lanes, s, &p);
+                               (r->opt.flags & TE_OPT_PROFILE) ? 1 : 0, lanes,
+                               want_fused(ctx, r->H, r->opt), s, &p);
             if (res == TE_OK) {
                 res = run_solve(ctx, r->H, p, s, r->v_in_dev, r->t, r->tol, r->opt, r->v_out_dev,
                                 true, &S, &r->cancel);

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <condition_variable>
 #include <deque>
@@ -28,6 +29,7 @@
 #define TE_BLOCK 256                 // threads per block of the streaming kernels
 #define TE_STEP_THREADS 256          // threads of the single-CTA step kernel
 #define TE_GAUSS_MAX 64
+#define TE_FUSED_SLICES_PER_WARP 4   // slices (of 32 rows) a warp of the fused Lanczos loop holds
 
 // Solver state in device memory, one per plan.  Written by the kernels of a
 // restart, read back by the host after each restart (a copy of the struct).
@@ -150,6 +152,10 @@ struct Plan {
     size_t bytes = 0;
     bool in_use = false;
     int grid_k1 = 0, grid_stream = 0, grid_reorth = 0;
+    // fused Lanczos loop (te_fused.cu): one cooperative kernel per restart
+    int fused = 0;
+    int fused_grid = 0, fused_threads = 0;
+    unsigned int* bar = nullptr;     // its grid-barrier words
 };
 
 struct te_ctx;
@@ -179,6 +185,7 @@ struct te_ctx {
     cudaEvent_t user_ev = nullptr;
     bool own_stream = false;
     int num_sms = 0;
+    int coop = 0;                    // device supports cooperative launches (fused Lanczos loop)
     std::string err;
     std::mutex mu;                   // plans, matrices
     std::vector<Plan*> plans;
@@ -233,6 +240,12 @@ cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double*
                              double* partials, cudaStream_t s);
 cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
                           double* dsum, int num_sms, cudaStream_t s);
+// fused Lanczos loop (te_fused.cu): shape of its cooperative grid (false: H too
+// large or without a sliced copy); the launch clears bar and runs m steps.
+bool fused_shape(const te_matrix* H, int num_sms, int* grid, int* threads);
+cudaError_t launch_lanczos_fused(const te_matrix* H, double2* V, double* S, DevState* st, int m,
+                                 double* part, unsigned int* bar, int grid, int threads,
+                                 cudaStream_t s);
 te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowptr, int64_t* nnz,
                       cudaStream_t s);
 

@@ -8,6 +8,25 @@
 
 namespace te_slices {
 
+// Loads of the vector being multiplied.  kL2 = false: through the read-only
+// path (the vector does not change during the launch).  kL2 = true: from L2,
+// for a kernel that reads vectors other blocks wrote earlier in the same launch
+// (the fused Lanczos loop), where a line held in another SM's L1 could be stale.
+template <bool kL2, class T>
+__device__ __forceinline__ T ldx(const T* p) {
+    if constexpr (kL2) return __ldcg(p);
+    else return __ldg(p);
+}
+
+// Loads of the stored matrix: streamed once per product (evict-first) in the
+// large-matrix kernels; kept cacheable in the fused loop, which re-reads the
+// whole (small) matrix at every Lanczos step.
+template <bool kL2, class T>
+__device__ __forceinline__ T ldm(const T* p) {
+    if constexpr (kL2) return __ldg(p);
+    else return __ldcs(p);
+}
+
 // Slice products of the two stored forms.  row() returns, for the lane's row of
 // slice s, the sums k1 = sum a (x + y), k2 = sum (b - a) x, k3 = sum (a + b) y
 // over its stored entries, combined as (k1 - k3, k1 + k2), plus the diagonal
@@ -17,6 +36,7 @@ struct FullSlices {
     const int32_t* __restrict__ col;
     const double* __restrict__ va;
     const double2* __restrict__ vpq;
+    template <bool kL2 = false>
     __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
                                            const double* __restrict__ xs, int64_t r,
                                            double2 xr) const {
@@ -35,14 +55,14 @@ struct FullSlices {
             double2 q[4], xv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                c[u] = __ldcs(cp + 32 * (k + u));
-                a[u] = __ldcs(ap + 32 * (k + u));
-                q[u] = __ldcs(qp + 32 * (k + u));
+                c[u] = ldm<kL2>(cp + 32 * (k + u));
+                a[u] = ldm<kL2>(ap + 32 * (k + u));
+                q[u] = ldm<kL2>(qp + 32 * (k + u));
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                xv[u] = __ldg(x + c[u]);
-                z[u] = __ldg(xs + c[u]);
+                xv[u] = ldx<kL2>(x + c[u]);
+                z[u] = ldx<kL2>(xs + c[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -53,11 +73,11 @@ struct FullSlices {
         }
 #pragma unroll 1
         for (; k < w; ++k) {
-            const double a0 = __ldcs(ap + 32 * k);
-            const double2 q0 = __ldcs(qp + 32 * k);
-            const int c0 = __ldcs(cp + 32 * k);
-            const double2 x0 = __ldg(x + c0);
-            const double z0 = __ldg(xs + c0);
+            const double a0 = ldm<kL2>(ap + 32 * k);
+            const double2 q0 = ldm<kL2>(qp + 32 * k);
+            const int c0 = ldm<kL2>(cp + 32 * k);
+            const double2 x0 = ldx<kL2>(x + c0);
+            const double z0 = ldx<kL2>(xs + c0);
             k1 = fma(a0, z0, k1);
             k2 = fma(q0.x, x0.x, k2);
             k3 = fma(q0.y, x0.y, k3);
@@ -73,6 +93,7 @@ struct IndexedSlices {
     const double* __restrict__ ta;
     const double2* __restrict__ tpq;
     const double* __restrict__ diag;
+    template <bool kL2 = false>
     __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
                                            const double* __restrict__ xs, int64_t r,
                                            double2 xr) const {
@@ -88,8 +109,8 @@ struct IndexedSlices {
             int c[4], q[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                c[u] = __ldcs(cp + 32 * (k + u));
-                q[u] = __ldcs(ip + 32 * (k + u));
+                c[u] = ldm<kL2>(cp + 32 * (k + u));
+                q[u] = ldm<kL2>(ip + 32 * (k + u));
             }
             double a[4], z[4];
             double2 p[4], xv[4];
@@ -97,8 +118,8 @@ struct IndexedSlices {
             for (int u = 0; u < 4; ++u) {
                 a[u] = __ldg(ta + q[u]);
                 p[u] = __ldg(tpq + q[u]);
-                xv[u] = __ldg(x + c[u]);
-                z[u] = __ldg(xs + c[u]);
+                xv[u] = ldx<kL2>(x + c[u]);
+                z[u] = ldx<kL2>(xs + c[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -109,17 +130,17 @@ struct IndexedSlices {
         }
 #pragma unroll 1
         for (; k < w; ++k) {
-            const int qq = __ldcs(ip + 32 * k);
-            const int cc = __ldcs(cp + 32 * k);
+            const int qq = ldm<kL2>(ip + 32 * k);
+            const int cc = ldm<kL2>(cp + 32 * k);
             const double a0 = __ldg(ta + qq);
             const double2 p0 = __ldg(tpq + qq);
-            const double2 x0 = __ldg(x + cc);
-            const double z0 = __ldg(xs + cc);
+            const double2 x0 = ldx<kL2>(x + cc);
+            const double z0 = ldx<kL2>(xs + cc);
             k1 = fma(a0, z0, k1);
             k2 = fma(p0.x, x0.x, k2);
             k3 = fma(p0.y, x0.y, k3);
         }
-        const double dg = r >= 0 ? __ldcs(diag + r) : 0.0;
+        const double dg = r >= 0 ? ldm<kL2>(diag + r) : 0.0;
         return make_double2(fma(dg, xr.x, k1 - k3), fma(dg, xr.y, k1 + k2));
     }
 };
@@ -134,6 +155,7 @@ struct RealIndexedSlices {
     const uint16_t* __restrict__ vidx;
     const double* __restrict__ ta;
     const double* __restrict__ diag;
+    template <bool kL2 = false>
     __device__ __forceinline__ double2 row(int64_t s, int lane, const double2* __restrict__ x,
                                            const double* __restrict__ /*xs*/, int64_t r,
                                            double2 xr) const {
@@ -148,15 +170,15 @@ struct RealIndexedSlices {
             int c[4], q[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                c[u] = __ldcs(cp + 32 * (k + u));
-                q[u] = __ldcs(ip + 32 * (k + u));
+                c[u] = ldm<kL2>(cp + 32 * (k + u));
+                q[u] = ldm<kL2>(ip + 32 * (k + u));
             }
             double a[4];
             double2 xv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 a[u] = __ldg(ta + q[u]);
-                xv[u] = __ldg(x + c[u]);
+                xv[u] = ldx<kL2>(x + c[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -166,14 +188,14 @@ struct RealIndexedSlices {
         }
 #pragma unroll 1
         for (; k < w; ++k) {
-            const int qq = __ldcs(ip + 32 * k);
-            const int cc = __ldcs(cp + 32 * k);
+            const int qq = ldm<kL2>(ip + 32 * k);
+            const int cc = ldm<kL2>(cp + 32 * k);
             const double a0 = __ldg(ta + qq);
-            const double2 x0 = __ldg(x + cc);
+            const double2 x0 = ldx<kL2>(x + cc);
             k1 = fma(a0, x0.x, k1);
             k2 = fma(a0, x0.y, k2);
         }
-        const double dg = r >= 0 ? __ldcs(diag + r) : 0.0;
+        const double dg = r >= 0 ? ldm<kL2>(diag + r) : 0.0;
         return make_double2(fma(dg, xr.x, k1), fma(dg, xr.y, k2));
     }
 };

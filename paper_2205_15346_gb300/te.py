@@ -45,6 +45,8 @@ TE_REORTH_FULL = 1
 TE_OPT_PROFILE = 0x10
 TE_SMALLEXP_CHEB = 0
 TE_SMALLEXP_EIG = 1
+TE_FUSED_AUTO = 0
+TE_FUSED_OFF = 1
 TE_MODEL_TFIM = 1
 TE_MODEL_XXZDM = 2
 TE_MODEL_BOSE = 3
@@ -56,7 +58,7 @@ class te_options(C.Structure):
                 ("reorth", C.c_int32), ("t_step0", C.c_double), ("shrink", C.c_double),
                 ("quad_rel_tol", C.c_double), ("quad_max_levels", C.c_int32),
                 ("max_substeps", C.c_int32), ("min_step_rel", C.c_double), ("flags", C.c_uint32),
-                ("spmv_lanes", C.c_int32), ("small_exp", C.c_int32), ("reserved", C.c_int32)]
+                ("spmv_lanes", C.c_int32), ("small_exp", C.c_int32), ("fused_lanczos", C.c_int32)]
 
 
 class te_stats(C.Structure):
@@ -66,7 +68,8 @@ class te_stats(C.Structure):
                 ("flags", C.c_uint32), ("m_used", C.c_int32), ("spmv_ms", C.c_double),
                 ("spmv_launches", C.c_int64), ("solve_ms", C.c_double),
                 ("quad_integrals", C.c_int64), ("quad_nodes", C.c_int64),
-                ("eig_mcycles", C.c_double), ("search_mcycles", C.c_double)]
+                ("eig_mcycles", C.c_double), ("search_mcycles", C.c_double),
+                ("fused_restarts", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -109,6 +112,8 @@ _SIGS = {
     "te_matrix_free": (None, [_P]),
     "te_matrix_tune": (C.c_int32, [_P, _P, C.c_int32, C.POINTER(C.c_double)]),
     "te_measure_fp64": (C.c_int32, [_P, C.POINTER(C.c_double)]),
+    "te_fused_barrier_check": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_double)]),
     "te_spmv": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_spmv_noalloc": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
     "te_evolve": (C.c_int32, [_P, _P, _P, C.c_double, C.c_double, C.c_int32,
@@ -344,6 +349,17 @@ def te_measure_fp64(ctx) -> float:
     r = C.c_double()
     _check(ctx, lib().te_measure_fp64(ctx, C.byref(r)))
     return r.value
+
+
+def te_fused_barrier_check(ctx, absent_block: int = -1) -> tuple:
+    """One grid barrier of the fused Lanczos loop with block `absent_block`
+    missing (-1: none).  Returns (status, blocks that passed, kernel ms); the
+    status is TE_ERR_TIMEOUT when the other blocks gave up waiting."""
+    n = C.c_int32()
+    ms = C.c_double()
+    st = _check(ctx, lib().te_fused_barrier_check(ctx, int(absent_block), C.byref(n), C.byref(ms)),
+                allow=(TE_OK, TE_ERR_TIMEOUT))
+    return st, n.value, ms.value
 
 
 def te_matrix_free(H) -> None:
