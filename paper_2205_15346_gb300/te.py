@@ -38,6 +38,8 @@ TE_WARN_QUAD = 0x2
 TE_FLAG_BREAKDOWN = 0x4
 TE_M_MAX = 128
 TE_NOALLOC_MAX_D = 8388608
+TE_BATCH_MAX = 64
+TE_MULTI_MAX = 256
 TE_QUAD_TANH_SINH = 0
 TE_QUAD_GAUSS = 1
 TE_REORTH_NONE = 0

@@ -70,3 +70,14 @@ def test_create_without_device_reports_error(libte):
     from paper_2205_15346_gb300 import te
     with pytest.raises(te.TEError):
         te.te_create(0, stream=0)
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define of include/te.h has the same value in the binding."""
+    from paper_2205_15346_gb300 import te
+    src = open(os.path.join(ROOT, "include", "te.h")).read()
+    defines = re.findall(r"^#define\s+(TE_[A-Z0-9_]+)\s+(-?(?:0x[0-9a-fA-F]+|\d+))u?\b", src, flags=re.M)
+    assert len(defines) > 30
+    for name, value in defines:
+        assert hasattr(te, name), name
+        assert getattr(te, name) == int(value, 0), name
