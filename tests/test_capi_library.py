@@ -81,3 +81,25 @@ def test_binding_constants_match_the_header():
     for name, value in defines:
         assert hasattr(te, name), name
         assert getattr(te, name) == int(value, 0), name
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes structures of the binding have the fields, order and types of
+    the header's structs (a mismatch would corrupt every call silently)."""
+    import ctypes as C
+
+    from paper_2205_15346_gb300 import te
+    src = open(os.path.join(ROOT, "include", "te.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    ctype = {"int32_t": C.c_int32, "int64_t": C.c_int64, "uint32_t": C.c_uint32,
+             "double": C.c_double}
+    structs = re.findall(r"typedef struct (te_[a-z_]+) \{(.*?)\} \1;", src, flags=re.S)
+    assert {n for n, _ in structs} >= {"te_options", "te_stats", "te_matrix_info",
+                                        "te_model_desc", "te_operator_desc"}
+    for name, body in structs:
+        fields = re.findall(r"^\s*(?:const\s+)?([a-z0-9_]+)\s*(\*?)\s*([a-zA-Z0-9_]+);", body, flags=re.M)
+        py = getattr(te, name)._fields_
+        assert [f[2] for f in fields] == [p[0] for p in py], name
+        for (typ, star, fname), (_, pytype) in zip(fields, py):
+            want = C.POINTER(ctype[typ]) if star else ctype[typ]
+            assert pytype == want, (name, fname)
