@@ -103,3 +103,34 @@ def test_binding_structs_match_the_header():
         for (typ, star, fname), (_, pytype) in zip(fields, py):
             want = C.POINTER(ctype[typ]) if star else ctype[typ]
             assert pytype == want, (name, fname)
+
+
+def test_binding_signatures_match_the_header():
+    """Each entry point's ctypes signature has the header's arity, return type
+    and scalar argument types (pointers may be typed or void)."""
+    import ctypes as C
+
+    from paper_2205_15346_gb300 import te
+    src = open(os.path.join(ROOT, "include", "te.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    scalar = {"int32_t": C.c_int32, "int64_t": C.c_int64, "uint32_t": C.c_uint32,
+              "double": C.c_double, "te_status": C.c_int32}
+    protos = re.findall(r"^\s*(?:const\s+)?([a-z_0-9]+)\s*(\*?)\s*(te_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
+                        src, flags=re.M)
+    assert len(protos) >= 30
+    for ret, rstar, name, args in protos:
+        restype, argtypes = te._SIGS[name]
+        if rstar:
+            assert restype in (C.c_char_p, C.c_void_p), name
+        elif ret == "void":
+            assert restype is None, name
+        else:
+            assert restype == scalar[ret], name
+        args = [a.strip() for a in args.split(",") if a.strip() and a.strip() != "void"]
+        assert len(args) == len(argtypes), name
+        for a, t in zip(args, argtypes):
+            if "*" in a:
+                assert t is C.c_void_p or hasattr(t, "contents") or t is C.c_char_p, (name, a)
+            else:
+                typ = a.replace("const ", "").split()[0]
+                assert t == scalar[typ], (name, a)
