@@ -267,3 +267,19 @@ def test_norm1_definition_and_roundoff_estimate():
     assert res.warn_roundoff == any(per > s[1] for s in res.steps)
     res = krylov.evolve(A, W.random_state(40, 256), 1.0, 1e-14, 20)
     assert res.warn_roundoff
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 40, 128])
+def test_eigensolver_residual_and_orthogonality(n):
+    """eig_hessenberg on random tridiagonals: ||T Q - Q Lambda|| <= 1e-13 ||T||,
+    Q orthogonal to 1e-13, eigenvalues ascending and equal to the dense
+    symmetric eigensolver's (a different LAPACK routine) to 1e-13 ||T||."""
+    u = W.uniform(700 + n, 2 * n)
+    alpha, beta = u[:n] * 4.0 - 2.0, u[n:2 * n - 1] + 0.1
+    lam, Q = krylov.eig_hessenberg(alpha, beta)
+    T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+    nt = np.linalg.norm(T, 2)
+    assert np.linalg.norm(T @ Q - Q * lam, 2) <= 1e-13 * nt
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 1e-13
+    assert np.all(np.diff(lam) >= 0)
+    assert np.max(np.abs(lam - np.linalg.eigvalsh(T))) <= 1e-13 * nt
