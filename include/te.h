@@ -295,9 +295,12 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y,
  *   d must not exceed TE_NOALLOC_MAX_D (else TE_ERR_UNSUPPORTED, nothing runs).
  * The reduction scratch is a fixed device array inside libte (about 64 KB),
  * which every GPU that loads the library keeps until the process exits.  The
- * first call on a device looks up that array's device address (a one-time
- * set-up step), so make the first call on each device before any stream
- * capture begins.  All calls on a device share the array and it keeps the last
+ * first call on a device is a set-up step: it looks up that array's device
+ * address, and under CUDA's lazy module loading (the default) it is also when
+ * the array and the kernel are loaded onto the device, which the driver may
+ * allocate for.  Later calls allocate nothing.  So make the first call on each
+ * device before any stream capture begins and before the caller's device
+ * footprint must stay fixed.  All calls on a device share the array and it keeps the last
  * call's contents: the library clears the part that must start at zero on every
  * call, but calls that overlap on the GPU (from other streams or other host
  * threads) race on it and must be serialised by the caller.  The call waits
@@ -313,7 +316,11 @@ te_status te_spmv_noalloc(te_ctx* ctx, const te_matrix* H, const double* x, doub
  * v_in and v_out may be the same buffer.  st may be NULL.
  * Errors: TE_ERR_INVALID_ARG, TE_ERR_NOT_NORMALIZED, TE_ERR_NONFINITE,
  * TE_ERR_STEP_UNDERFLOW (v_out then holds the state at st->t_reached),
- * TE_ERR_UNSUPPORTED, TE_ERR_INTERNAL, TE_ERR_CUDA, TE_ERR_OOM. */
+ * TE_ERR_UNSUPPORTED (also: after a lucky breakdown, which takes the whole
+ * remaining time in one step, the default Chebyshev small exponential splits
+ * that step into pieces of a ||H_m|| tau <= 2048 and accepts at most 512 of
+ * them; TE_SMALLEXP_EIG has no such limit), TE_ERR_INTERNAL, TE_ERR_CUDA,
+ * TE_ERR_OOM. */
 te_status te_evolve(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
                     int32_t m, const te_options* opt, double* v_out, te_stats* st);
 

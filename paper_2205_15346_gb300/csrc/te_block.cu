@@ -823,6 +823,8 @@ te_status run_block_solve(te_ctx* ctx, const te_matrix* H, int nvec, const doubl
         set_error(ctx, worst, "non-finite values in a batched solve");
     else if (worst == TE_ERR_STEP_UNDERFLOW)
         set_error(ctx, worst, "step size underflow in a batched solve");
+    else if (worst == TE_ERR_UNSUPPORTED)
+        set_error(ctx, worst, kSeriesRangeMsg);
     else if (worst != TE_OK)
         set_error(ctx, worst, "batched solve failed on the device");
     const double el = now_ms() - t0;

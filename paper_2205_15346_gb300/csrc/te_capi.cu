@@ -375,7 +375,8 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
                                            ? "step size underflow: no step meets the error rate"
                                        : result == TE_ERR_TIMEOUT
                                            ? "a grid barrier of the fused Lanczos loop gave up waiting"
-                                           : "solver failed on the device");
+                                       : result == TE_ERR_UNSUPPORTED ? kSeriesRangeMsg
+                                                                      : "solver failed on the device");
                 break;
             }
             if (h->done) break;

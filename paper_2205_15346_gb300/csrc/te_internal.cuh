@@ -286,6 +286,11 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
 void gauss_legendre_table(int n, double* x, double* w);
 
 te_status set_error(te_ctx* ctx, te_status s, const std::string& msg);
+// Device status TE_ERR_UNSUPPORTED from the step or sample kernel: exp(-i H_m tau) e_1
+// after a lucky breakdown needed more series pieces than the build allows.
+constexpr const char* kSeriesRangeMsg =
+    "exp(-i H_m tau) e_1 beyond the Chebyshev series' range (a lucky breakdown with "
+    "||H_m|| |t| above ~1e6); TE_SMALLEXP_EIG evaluates any tau";
 te_status cuda_error(te_ctx* ctx, cudaError_t e, const char* what);
 
 #define TE_CUDA_TRY(ctx, call)                                   \

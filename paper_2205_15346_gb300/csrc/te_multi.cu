@@ -726,6 +726,8 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
         set_error(ctx, worst, "non-finite values in a grouped solve");
     else if (worst == TE_ERR_STEP_UNDERFLOW)
         set_error(ctx, worst, "step size underflow in a grouped solve");
+    else if (worst == TE_ERR_UNSUPPORTED)
+        set_error(ctx, worst, kSeriesRangeMsg);
     else if (worst != TE_OK)
         set_error(ctx, worst, "grouped solve failed on the device");
     release();

@@ -106,7 +106,13 @@ __global__ void __launch_bounds__(TE_STEP_THREADS) k_sample_omega(DevState* st, 
     for (int s = lo + blockIdx.x; s < hi; s += gridDim.x) {
         const double tau = fmax(ts[s] - st->win_t0, 0.0);
         __syncthreads();
-        cheb_exp_e1(al, be, n, a, b, inv_a, tau, jk, v3, mcap, &sh_S, om);
+        if (!cheb_exp_e1(al, be, n, a, b, inv_a, tau, jk, v3, mcap, &sh_S, om)) {
+            if (threadIdx.x == 0) {
+                st->status = TE_ERR_UNSUPPORTED;   // sample beyond the series' pieces
+                st->done = 1;
+            }
+            return;
+        }
         __syncthreads();
         for (int r = tid; r < n; r += nt) {
             const double sc = beta0 * st->scale[r];

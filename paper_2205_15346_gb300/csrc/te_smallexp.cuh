@@ -21,53 +21,32 @@ __device__ __forceinline__ int bessel_terms(double z) {
     return (int)ceil(z + 10.0 * cbrt(z) + 30.0);
 }
 
-// om[0..n) = exp(-i T tau) e_1.  T: diagonal al, off-diagonal be (be[n-1] unused),
-// n <= blockDim.x.  Called by every thread of the block with the same arguments;
-// jk: kKcap shared doubles, v3: 3 mcap shared doubles, sh_S: one shared double.
-__device__ __forceinline__ void cheb_exp_e1(const double* al, const double* be, int n, double a,
-                                            double b, double inv_a, double tau, double* jk,
-                                            double* v3, int mcap, double* sh_S, double2* om) {
+// Largest argument z = a tau the series takes in one piece (K(2048) = 2205 terms,
+// well inside kKcap), and the most pieces one call may take.  A longer tau is
+// split into p equal pieces, exp(-i T tau) = (exp(-i T tau / p))^p, each piece
+// applied to the previous piece's complex result: exact on the Krylov space, so
+// a lucky breakdown (which takes the whole remaining time in one step, Sec. 2.4)
+// may evaluate any tau without truncating the series.  Beyond kMaxPieces pieces
+// (z > 2048 x 512) the call reports failure instead of truncating.
+constexpr double kZPiece = 2048.0;
+constexpr int kMaxPieces = 512;
+
+// One application of the truncated series to a real vector x (x = e_1 when
+// u == nullptr, else x_i = Re u_i (part 0) or Im u_i (part 1)):
+//   (accr + i acci) = sum_{k<=K} c_k (-i)^k J_k T_k(T~) x,   row tid of the result.
+// jk[0..K] holds J_k unnormalised; invS is the normalisation.  n <= blockDim.x.
+__device__ __forceinline__ void cheb_pass(const double* al, const double* be, int n, double b,
+                                          double inv_a, int K, const double* jk, double invS,
+                                          double* v3, int mcap, const double2* u, int part,
+                                          double* accr_out, double* acci_out) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const double z = a * tau;
-    const int K = min(bessel_terms(fmin(z, (double)kKcap)), kKcap - kMillerExtra - 1);
-    const int M = K + kMillerExtra;
-    if (tid == 0) {
-        // J_0..J_K(z) by Miller's backward recurrence, normalised by J_0 + 2 sum J_2k
-        double* J = jk;
-        if (!(z > 1e-300)) {
-            J[0] = 1.0;
-            for (int k = 1; k <= K; ++k) J[k] = 0.0;
-            (*sh_S) = 1.0;
-        } else {
-            const double inv = 2.0 / z;
-            double t = inv * M, jp = 0.0, jc = 1e-300, S = 0.0;
-            for (int k = M; k >= 0; --k) {
-                if (k <= K) J[k] = jc;
-                if ((k & 1) == 0) S += (k == 0) ? jc : 2.0 * jc;
-                if (k == 0) break;
-                const double jn = fma(t, jc, -jp);
-                jp = jc;
-                jc = jn;
-                t -= inv;
-                if (fabs(jc) > kBig) {
-                    jc *= kSmall;
-                    jp *= kSmall;
-                    S *= kSmall;
-                    for (int q = k; q <= K; ++q) J[q] *= kSmall;
-                }
-            }
-            (*sh_S) = S;
-        }
-    }
-    __syncthreads();
-    const double invS = 1.0 / (*sh_S);
-    // sum_k c_k (-i)^k J_k T_k(T~) e_1, recomputing the Chebyshev vectors
     double* v0 = v3;
     double* v1 = v3 + mcap;
     double* v2 = v3 + 2 * mcap;
     double accr = 0.0, acci = 0.0;
+    __syncthreads();
     for (int i = tid; i < n; i += nt) {
-        v0[i] = (i == 0) ? 1.0 : 0.0;
+        v0[i] = (u == nullptr) ? ((i == 0) ? 1.0 : 0.0) : (part == 0 ? u[i].x : u[i].y);
         v2[i] = 0.0;
     }
     __syncthreads();
@@ -99,7 +78,89 @@ __device__ __forceinline__ void cheb_exp_e1(const double* al, const double* be, 
         vc = vn;
         vn = tmp;
     }
+    *accr_out = accr;
+    *acci_out = acci;
+}
+
+// om[0..n) = exp(-i T tau) e_1.  T: diagonal al, off-diagonal be (be[n-1] unused),
+// n <= blockDim.x.  Called by every thread of the block with the same arguments;
+// jk: kKcap shared doubles, v3: 3 mcap shared doubles, sh_S: one shared double.
+// n = 1 takes the closed form e^{-i al_0 tau}.  Returns false (every thread, om
+// untouched) when a tau would need more than kMaxPieces pieces.
+__device__ __forceinline__ bool cheb_exp_e1(const double* al, const double* be, int n, double a,
+                                            double b, double inv_a, double tau, double* jk,
+                                            double* v3, int mcap, double* sh_S, double2* om) {
+    const int tid = threadIdx.x;
+    if (n == 1) {
+        if (tid == 0) {
+            double s, c;
+            sincos(al[0] * tau, &s, &c);
+            om[0] = make_double2(c, -s);
+        }
+        return true;
+    }
+    int p = 1;
+    if (a * tau > kZPiece) {
+        const double pf = ceil(a * tau / kZPiece);
+        if (!(pf <= (double)kMaxPieces)) return false;
+        p = (int)pf;
+    }
+    const double tp = (p == 1) ? tau : tau / p;          // one piece
+    const double z = a * tp;
+    const int K = min(bessel_terms(fmin(z, (double)kKcap)), kKcap - kMillerExtra - 1);
+    const int M = K + kMillerExtra;
+    __syncthreads();
+    if (tid == 0) {
+        // J_0..J_K(z) by Miller's backward recurrence, normalised by J_0 + 2 sum J_2k.
+        // The coefficient 2k/z is formed from k at every step: decrementing it
+        // by 2/z instead accumulates one rounding per step, which shifts the
+        // phase of the oscillating J_k (k < z) by ~1e-11 at z = 2000.
+        double* J = jk;
+        if (!(z > 1e-300)) {
+            J[0] = 1.0;
+            for (int k = 1; k <= K; ++k) J[k] = 0.0;
+            (*sh_S) = 1.0;
+        } else {
+            const double inv = 2.0 / z;
+            double t = inv * M, jp = 0.0, jc = 1e-300, S = 0.0;
+            for (int k = M; k >= 0; --k) {
+                if (k <= K) J[k] = jc;
+                if ((k & 1) == 0) S += (k == 0) ? jc : 2.0 * jc;
+                if (k == 0) break;
+                const double jn = fma(t, jc, -jp);
+                jp = jc;
+                jc = jn;
+                t = inv * (double)(k - 1);    // from the index: a running t -= inv drifts
+                if (fabs(jc) > kBig) {
+                    jc *= kSmall;
+                    jp *= kSmall;
+                    S *= kSmall;
+                    for (int q = k; q <= K; ++q) J[q] *= kSmall;
+                }
+            }
+            (*sh_S) = S;
+        }
+    }
+    __syncthreads();
+    const double invS = 1.0 / (*sh_S);
     double sb, cb;
-    sincos(b * tau, &sb, &cb);                // e^{-i b tau}
-    if (tid < n) om[tid] = make_double2(cb * accr + sb * acci, cb * acci - sb * accr);
+    sincos(b * tp, &sb, &cb);                 // e^{-i b tp}
+    // first piece from e_1
+    double accr, acci;
+    cheb_pass(al, be, n, b, inv_a, K, jk, invS, v3, mcap, nullptr, 0, &accr, &acci);
+    double2 r = make_double2(cb * accr + sb * acci, cb * acci - sb * accr);
+    // later pieces from the previous result u = x + i y:
+    //   S(u) = S(x) + i S(y), S the real-coefficient series applied to a real vector
+    for (int q = 1; q < p; ++q) {
+        __syncthreads();
+        if (tid < n) om[tid] = r;
+        double xr, xi, yr, yi;
+        cheb_pass(al, be, n, b, inv_a, K, jk, invS, v3, mcap, om, 0, &xr, &xi);
+        cheb_pass(al, be, n, b, inv_a, K, jk, invS, v3, mcap, om, 1, &yr, &yi);
+        const double sr = xr - yi, si = xi + yr;
+        r = make_double2(cb * sr + sb * si, cb * si - sb * sr);
+    }
+    __syncthreads();
+    if (tid < n) om[tid] = r;
+    return true;
 }

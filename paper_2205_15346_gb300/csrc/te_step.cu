@@ -184,6 +184,9 @@ __device__ __forceinline__ double f_cheb(const Small& F, double tau) {
         }
         TE_GUARD()
         for (; k >= 3; k -= 4) {
+            // 2k/z from the index once per group: the running t -= inv drifts by one
+            // rounding per step, which would shift the phase of J_k at large z
+            t = inv * (double)k;
             TE_ACC(k, 3)
             TE_REC()
             TE_ACC(k - 1, 2)
@@ -669,8 +672,15 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
             }
             L.om[r] = make_double2(re, im);
         }
-    } else {
-        cheb_exp_e1(L.al, L.be, n, F.a, F.b, F.inv_a, tau, L.jk, L.v3, mcap, &sh_S, L.om);
+    } else if (!cheb_exp_e1(L.al, L.be, n, F.a, F.b, F.inv_a, tau, L.jk, L.v3, mcap, &sh_S,
+                            L.om)) {
+        // a step longer than the series' pieces reach (only a lucky breakdown takes one)
+        if (tid == 0) {
+            st->status = TE_ERR_UNSUPPORTED;
+            st->done = 1;
+            st->quad_warnings += sh_warn;
+        }
+        return;
     }
     __syncthreads();
     for (int r = tid; r < n; r += nt) {
