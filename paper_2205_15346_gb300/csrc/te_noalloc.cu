@@ -10,8 +10,11 @@
 // partial sum per thread block, an arrival counter and the result slot) lives
 // in a fixed, file-scope device array instead of memory allocated per call.
 //
-// That array is created when the library is loaded on a GPU and stays there
-// until the process exits.  Its size caps the problem: one block covers
+// Under CUDA's lazy module loading (the default) the array and the kernel are
+// loaded onto a device at the first call there: that first call, which also
+// looks up the array's device address, may allocate through the driver and is
+// the set-up step; later calls on the device allocate nothing.  The array then
+// stays on the device until the process exits.  Its size caps the problem: one block covers
 // kRowsPerBlock rows and the array has room for kMaxBlocks partials, so d may
 // be at most TE_NOALLOC_MAX_D.  All calls on a device share the one array and
 // it keeps the last call's contents, so the arrival counter is cleared on the
