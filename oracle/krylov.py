@@ -204,14 +204,16 @@ def krylov_exponential(lam, Q, tau: float):
 
 
 def evolve(H, v, t: float, tol: float, m: int, opt: Options | None = None,
-           max_restarts: int | None = None, samples=None) -> EvolveResult:
+           max_restarts: int | None = None, samples=None, threads: int | None = None) -> EvolveResult:
     """exp(-iHt) v by Algorithm 1 (restarted Lanczos with the integral error bound).
 
     H: scipy sparse (or dense) Hermitian d x d; v: normalised complex vector.
     max_restarts bounds the work for timing samples (t_reached then tells how far
     the solve got).  samples: optional times with the sign of t, |s| <= |t|,
     non-decreasing in |s|; the states at those times are returned in
-    res.samples (see the module docstring).
+    res.samples (see the module docstring).  threads: None takes scipy's
+    product; a count takes the plain C product of csrmv.c on that many threads
+    (the same definition; bitwise the same result for any count).
     """
     opt = opt or Options()
     v = np.asarray(v, dtype=np.complex128)
@@ -221,6 +223,9 @@ def evolve(H, v, t: float, tol: float, m: int, opt: Options | None = None,
     res.samples = [None] * len(sabs)
     res.sample_bounds = [0.0] * len(sabs)
     per_restart = d * norm1(H) * EPS                    # eq. numericalError
+    if threads is not None:
+        from .native import ThreadedCSR
+        H = ThreadedCSR(H, threads)
     if t == 0.0:
         for k in range(len(sabs)):
             res.samples[k] = res.v.copy()

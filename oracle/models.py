@@ -217,6 +217,74 @@ def bose_csr(p: dict, basis: BoseBasis | None = None) -> CSR:
     return CSR(d, rowptr, np.concatenate(cols), np.concatenate(vals))
 
 
+def _desc_rank(keys_desc: np.ndarray, targets: np.ndarray) -> np.ndarray:
+    """Positions of `targets` in the strictly decreasing array `keys_desc`
+    (every target must be present)."""
+    asc = keys_desc[::-1]
+    pos = np.searchsorted(asc, targets)
+    if not np.all(asc[np.minimum(pos, asc.size - 1)] == targets):
+        raise ValueError("target state outside the basis")
+    return keys_desc.size - 1 - pos
+
+
+def _rows_to_csr(d: int, rows, cols, vals) -> CSR:
+    """Entries ordered by (row, column); every (row, column) occurs once."""
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    if rows.size > 1 and np.any((rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])):
+        raise ValueError("duplicate entry")
+    rowptr = np.zeros(d + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(np.bincount(rows, minlength=d))
+    return CSR(d, rowptr, cols.astype(np.int64), vals)
+
+
+def bose_csr_vec(p: dict, basis: BoseBasis | None = None) -> CSR:
+    """The matrix of bose_csr, built with array operations over all rows at once.
+
+    For every ordered mode pair (i, j), i != j, each row n with n_i > 0 gets the
+    entry sqrt(n_i) sqrt(n_j + 1) c_ij at the rank of n - e_i + e_j (ranks from
+    the base-(N+1) key of the occupation tuple, which decreases along the
+    descending lexicographic basis); the diagonal is sum_i U_i n_i^2 added in
+    mode order.  The roundings are bose_row's, so the two are bitwise equal
+    (pinned in tests/test_oracle_models.py)."""
+    K, N = p["K"], p["N"]
+    basis = basis or BoseBasis(K, N)
+    c_re, c_im, U = p["c_re"], p["c_im"], p["U"]
+    S = np.array(basis.states, dtype=np.int64)                 # d x K
+    d = S.shape[0]
+    pw = (N + 1) ** np.arange(K - 1, -1, -1, dtype=np.int64)
+    keys = S @ pw
+    if d > 1 and not np.all(keys[1:] < keys[:-1]):
+        raise ValueError("basis is not in descending lexicographic order")
+    r = np.arange(d, dtype=np.int64)
+    acc = np.zeros(d)
+    for i in range(K):
+        acc = acc + U[i] * (S[:, i] * S[:, i]).astype(np.float64)
+    rows, cols, vals = [r], [r], [acc.astype(np.complex128)]
+    for i in range(K):
+        src = S[:, i] > 0
+        for j in range(K):
+            if j == i:
+                continue
+            rr = r[src]
+            col = _desc_rank(keys, keys[src] + pw[j] - pw[i])
+            amp = np.sqrt(S[src, i].astype(np.float64)) * np.sqrt((S[src, j] + 1).astype(np.float64))
+            if i < j:
+                cr, ci = c_re[_pair(K, i, j)], c_im[_pair(K, i, j)]
+            else:
+                cr, ci = c_re[_pair(K, j, i)], -c_im[_pair(K, j, i)]
+            v = np.empty(rr.size, dtype=np.complex128)
+            v.real = cr * amp
+            v.imag = ci * amp
+            rows.append(rr)
+            cols.append(col)
+            vals.append(v)
+    return _rows_to_csr(d, rows, cols, vals)
+
+
 def build(p: dict) -> CSR:
     """Dispatch on the parameter table's model name."""
     if p["model"] == "tfim":
@@ -357,6 +425,63 @@ def memory_csr(p: dict, basis: MemoryBasis | None = None) -> CSR:
     rowptr = np.zeros(d + 1, dtype=np.int64)
     rowptr[1:] = np.cumsum(lens)
     return CSR(d, rowptr, np.concatenate(cols), np.concatenate(vals))
+
+
+def memory_csr_vec(p: dict, basis: MemoryBasis | None = None) -> CSR:
+    """The matrix of memory_csr, built with array operations over all rows at once.
+
+    Row (b, q) (n0 = N0 - b, qubit tuple q) holds the diagonal, the two boson
+    hops to blocks b + 1 (n0 - 1) and b - 1 (m0 - 1), and one qubit hop per pair
+    a < b' with q_a != q_b' to the swapped tuple in the same block.  The qubit
+    hops' targets are found once per qubit tuple (the same in every block).  The
+    roundings are memory_row's, so the two are bitwise equal (pinned in
+    tests/test_oracle_models.py)."""
+    basis = basis or MemoryBasis(p)
+    K, Q, N0 = p["K"], p["K"] + p["Kp"], p["N0"]
+    em, Nc, dNc, C0, Cm = p["em"], p["Nc"], p["dNc"], p["C0"], p["Cm"]
+    qc = np.array(basis.qconf, dtype=np.int64)                 # nq x Q
+    nq = qc.shape[0]
+    d = len(basis)
+    pw = 2 ** np.arange(Q - 1, -1, -1, dtype=np.int64)
+    qkeys = qc @ pw                                            # decreasing along the basis
+    n1 = qc[:, :K].sum(axis=1)
+    n2 = qc[:, K:].sum(axis=1)
+    hop_src, hop_dst, hop_val = [], [], []
+    qi = np.arange(nq, dtype=np.int64)
+    for a in range(Q):
+        for b2 in range(a + 1, Q):
+            diff = qc[:, a] != qc[:, b2]
+            tk = qkeys[diff] + (qc[diff, b2] - qc[diff, a]) * pw[a] + (qc[diff, a] - qc[diff, b2]) * pw[b2]
+            hop_src.append(qi[diff])
+            hop_dst.append(_desc_rank(qkeys, tk))
+            hop_val.append(np.full(int(diff.sum()), complex(Cm * p["f"][_qpair(Q, a, b2)], 0.0)))
+    hop_src = np.concatenate(hop_src)
+    hop_dst = np.concatenate(hop_dst)
+    hop_val = np.concatenate(hop_val)
+    rows, cols, vals = [], [], []
+    for blk in range(N0 + 1):
+        n0 = N0 - blk
+        m0 = N0 - n0
+        base = blk * nq
+        diag = (em * (1.0 - n0 / Nc)) * n1.astype(np.float64) + \
+               (em * (1.0 - n0 / (Nc - dNc))) * n2.astype(np.float64)
+        rows.append(base + qi)
+        cols.append(base + qi)
+        vals.append(diag.astype(np.complex128))
+        if n0 >= 1:
+            amp = math.sqrt(float(n0)) * math.sqrt(float(m0 + 1))
+            rows.append(base + qi)
+            cols.append(base + nq + qi)
+            vals.append(np.full(nq, complex(C0 * amp, 0.0)))
+        if m0 >= 1:
+            amp = math.sqrt(float(m0)) * math.sqrt(float(n0 + 1))
+            rows.append(base + qi)
+            cols.append(base - nq + qi)
+            vals.append(np.full(nq, complex(C0 * amp, 0.0)))
+        rows.append(base + hop_src)
+        cols.append(base + hop_dst)
+        vals.append(hop_val)
+    return _rows_to_csr(d, rows, cols, vals)
 
 
 def memory_norm1(p: dict, basis: MemoryBasis | None = None) -> float:

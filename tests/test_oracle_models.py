@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import models
+from oracle import krylov, models
 
 I2 = np.eye(2)
 SZ_PAULI = np.diag([1.0, -1.0])            # bit 0 = up (+1), bit 1 = down (-1)
@@ -184,3 +184,51 @@ def test_coo_to_csr_duplicates_in_input_order():
     # explicit zeros are kept, empty rows allowed
     csr = models.coo_to_csr(4, [3, 0], [3, 0], [0.0, 1.0])
     assert list(csr.rowptr) == [0, 1, 1, 1, 2] and csr.val[1] == 0.0
+
+
+@pytest.mark.parametrize("K,N", [(6, 4), (8, 5), (10, 5), (14, 1)])
+def test_bose_vectorised_builder_is_bitwise_the_row_builder(K, N):
+    """bose_csr_vec (array form, used at full size) equals bose_csr row by row, bit for bit."""
+    p = W.bose_params(K, N, seed=60 + K)
+    a, b = models.bose_csr(p), models.bose_csr_vec(p)
+    assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val.view(np.uint64), b.val.view(np.uint64))
+
+
+def test_bose_vectorised_builder_full_size_sampled_rows():
+    """Config 4 size (K = 14, N = 10, d = 1,144,066): sampled rows of the array
+    form equal bose_row bit for bit, and the row lengths span 14..131."""
+    wl = W.workload("bose_K14_N10")
+    b = models.bose_csr_vec(wl["params"])
+    assert b.d == 1144066 and b.nnz == 91674506
+    lens = np.diff(b.rowptr)
+    assert lens.min() == 14 and lens.max() == 131
+    basis = models.BoseBasis(14, 10)
+    for r in (0, 1, 777, 123456, 654321, b.d - 2, b.d - 1):
+        c, v = models.bose_row(wl["params"], basis, r)
+        lo, hi = b.rowptr[r], b.rowptr[r + 1]
+        assert np.array_equal(c, b.col[lo:hi])
+        assert np.array_equal(v.view(np.uint64), b.val[lo:hi].view(np.uint64))
+
+
+@pytest.mark.parametrize("kw", [{}, {"K": 6, "Kp": 6, "N0": 30, "Nm": 3, "Nc": 30.0}])
+def test_memory_vectorised_builder_is_bitwise_the_row_builder(kw):
+    p = W.memory_params(**kw)
+    a, b = models.memory_csr(p), models.memory_csr_vec(p)
+    assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val.view(np.uint64), b.val.view(np.uint64))
+
+
+def test_threaded_product_is_the_plain_product():
+    """The oracle's C product (csrmv.c) on 1 and 4 threads: bitwise the same, and
+    equal to scipy's product to rounding (1e-15 (|A||x|)_i)."""
+    from oracle import native
+    A = models.build(W.bose_params(8, 5, seed=70)).to_scipy()
+    x = W.complex_gaussian(71, A.shape[0])
+    y1 = native.ThreadedCSR(A, 1) @ x
+    y4 = native.ThreadedCSR(A, 4) @ x
+    assert np.array_equal(y1, y4)
+    assert np.all(np.abs(y1 - A @ x) <= 1e-15 * (abs(A) @ np.abs(x)))
+    r1 = krylov.evolve(A, W.random_state(72, A.shape[0]), 3.0, 1e-8, 20, threads=1)
+    r4 = krylov.evolve(A, W.random_state(72, A.shape[0]), 3.0, 1e-8, 20, threads=4)
+    assert np.array_equal(r1.v, r4.v)
