@@ -5,6 +5,8 @@ must meet the same bar as a single solve: within 2 tol + 1e-12 of the oracle,
 within its own reported bound of the dense exp(-iHt)v, and equal within
 2 tol + 1e-12 to te_evolve on the same vector.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -172,7 +174,8 @@ def test_batch_rejects_reorth(te, ctx):
 def test_batch_full_size_xxzdm_L20_x64(te, ctx):
     """The 64-vector L = 20 workload as the benchmark runs it: every vector keeps
     its norm and energy (Sec. 1.1: exp(-iHt) is unitary and commutes with H),
-    reports a bound within tol, and two sampled vectors equal te_evolve."""
+    reports a bound within tol, two sampled vectors equal te_evolve, and vector 0
+    equals the oracle within 2 tol + 1e-12."""
     import torch
     wl = W.workload("batch_xxzdm_L20_x64")
     H = te.te_build_model(ctx, wl["params"])
@@ -192,3 +195,7 @@ def test_batch_full_size_xxzdm_L20_x64(te, ctx):
             assert torch.linalg.vector_norm(single - out[b]).item() <= 2 * wl["tol"] + 1e-12
     finally:
         te.te_matrix_free(H)
+    # vector 0 against the oracle (its product on all host cores), element by element
+    ref = krylov.evolve(models.xxzdm_csr(wl["params"]).to_scipy(), V0[0].cpu().numpy(), wl["t"],
+                        wl["tol"], wl["m"], threads=os.cpu_count())
+    assert np.linalg.norm(out[0].cpu().numpy() - ref.v) <= 2 * wl["tol"] + 1e-12

@@ -6,6 +6,7 @@ sequences may differ (sin/cos rounding can flip an accept/reject), so they
 are not compared.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -241,6 +242,43 @@ def test_xxzdm_L22_one_restart_against_oracle(te, ctx):
         te.te_matrix_free(H)
     ref = krylov.evolve(models.xxzdm_csr(p).to_scipy(), v0, 0.4, wl["tol"], wl["m"])
     assert ref.restarts == 1
+    assert np.linalg.norm(vg - ref.v) <= 2 * wl["tol"] + 1e-12
+
+
+def test_xxzdm_L22_several_restarts_against_oracle(te, ctx):
+    """Full-size XXZ-DM (d = 4,194,304) over t = 5 (several restarts, with the
+    shrink and growth of the step search between them), element by element
+    against the oracle (its product on all host cores)."""
+    wl = W.workload("xxzdm_L22")
+    p = wl["params"]
+    v0 = W.initial_vector(wl["v0"], wl["d"])
+    H = te.te_build_model(ctx, p)
+    try:
+        vg, st, _ = gpu_evolve(te, ctx, H, v0, 5.0, wl["tol"], wl["m"])
+    finally:
+        te.te_matrix_free(H)
+    ref = krylov.evolve(models.xxzdm_csr(p).to_scipy(), v0, 5.0, wl["tol"], wl["m"],
+                        threads=os.cpu_count())
+    assert ref.restarts >= 3 and st["restarts"] >= 3
+    assert np.linalg.norm(vg - ref.v) <= 2 * wl["tol"] + 1e-12
+
+
+def test_bose_K14_N10_restarts_against_oracle(te, ctx):
+    """Full-size bosonic workload (d = 1,144,066, rows of 14..131 entries, the
+    value-indexed copy with ~4,900 distinct couplings), tol = 1e-10, m = 50, over
+    a time of two to three restarts, element by element against the oracle."""
+    wl = W.workload("bose_K14_N10")
+    p = wl["params"]
+    b = models.BoseBasis(14, 10)
+    v0 = W.basis_state(wl["d"], b.index[wl["v0"][1]])
+    H = te.te_build_model(ctx, p)
+    try:
+        vg, st, _ = gpu_evolve(te, ctx, H, v0, 0.6, wl["tol"], wl["m"])
+    finally:
+        te.te_matrix_free(H)
+    A = models.bose_csr_vec(p, b).to_scipy()
+    ref = krylov.evolve(A, v0, 0.6, wl["tol"], wl["m"], threads=os.cpu_count())
+    assert ref.restarts >= 2 and st["restarts"] >= 2
     assert np.linalg.norm(vg - ref.v) <= 2 * wl["tol"] + 1e-12
 
 

@@ -4,6 +4,8 @@ Every problem is its own solve of Algorithm 1, so each result meets the single
 solve's bar: within 2 tol + 1e-12 of the oracle and within its reported bound
 of the dense exp(-iHt)v, whatever else runs in the same group.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -133,7 +135,8 @@ def test_multi_more_than_group_and_deterministic(te, ctx):
 
 def test_multi_full_size_tfim_x32(te, ctx):
     """The 32-chain workload as the benchmark runs it: norms and energies kept,
-    bounds within tol, sampled problems equal to te_evolve."""
+    bounds within tol, sampled problems equal to te_evolve, and the largest
+    problem equal to the oracle within 2 tol + 1e-12."""
     import torch
     wl = W.workload("tfim_multi_x32")
     probs = wl["problems"]
@@ -153,6 +156,12 @@ def test_multi_full_size_tfim_x32(te, ctx):
             assert abs(e1 - e0) <= 1e-6 * max(1.0, abs(e0))
             single, _, _ = te.te_evolve(ctx, Hs[i], v0[i], ts[i], wl["tol"], wl["m"])
             assert torch.linalg.vector_norm(single - outs[i]).item() <= 2 * wl["tol"] + 1e-12
+        # the largest problem (and, among the largest, the longest time) against the oracle
+        big = max(range(len(probs)), key=lambda i: (probs[i]["d"], probs[i]["t"]))
+        q = probs[big]
+        ref = krylov.evolve(models.build(q["params"]).to_scipy(), v0[big].cpu().numpy(), q["t"],
+                            wl["tol"], wl["m"], threads=os.cpu_count())
+        assert np.linalg.norm(outs[big].cpu().numpy() - ref.v) <= 2 * wl["tol"] + 1e-12
     finally:
         for H in Hs:
             te.te_matrix_free(H)
