@@ -29,6 +29,7 @@
 #ifndef TE_H_
 #define TE_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -192,6 +193,40 @@ typedef struct te_request te_request;
  * stream).  The context owns its device workspace (Krylov bases, reduction
  * scratch, captured CUDA graphs) and frees it in te_destroy. */
 te_status te_create(te_ctx** out, int32_t device, void* cuda_stream);
+
+/* A caller-supplied allocator for the library's device memory.  Sec. 2.1 of the
+ * paper states the problem as (H, v, t, err_max, m) and says nothing about where
+ * the solver's memory comes from; this hook lets a caller that owns device
+ * memory through its own pool (a framework's caching allocator, a service with
+ * a fixed budget) supply every device buffer the library uses: the CSR arrays
+ * and sliced copies of its matrices, the Krylov bases and solver state of its
+ * plans (the (m+1) d complex128 basis is the large one: 2.75 GB at d = 2^22,
+ * m = 40), the buffers of asynchronous requests and the temporaries of the
+ * builders.  Pinned host memory for the per-restart state copies still comes
+ * from cudaMallocHost, and te_spmv_noalloc's fixed scratch is not allocated.
+ *   alloc(user, bytes, device, stream): return `bytes` bytes of device memory
+ *     on `device`, aligned to at least 256 bytes, or NULL (the calling function
+ *     then fails with TE_ERR_OOM).  `stream` is the context's stream, on which
+ *     the library orders its work (requests run on per-worker streams and
+ *     synchronise them before their memory is released).
+ *   free(user, ptr, device, stream): release a pointer that alloc returned.  The
+ *     library synchronises the context's stream before every free, and frees
+ *     only memory whose work has finished, so a pool may reuse it at once.
+ * Both may be called from the calling thread and from the request scheduler's
+ * worker threads (te_submit), never concurrently for the same pointer.  A
+ * matrix or plan keeps using the allocator of the context that made it; free
+ * matrices and requests before destroying their context. */
+typedef struct te_allocator {
+    void* (*alloc)(void* user, size_t bytes, int32_t device, void* stream);
+    void (*free)(void* user, void* ptr, int32_t device, void* stream);
+    void* user;
+} te_allocator;
+
+/* te_create with a caller-supplied device allocator (NULL, or alloc == NULL:
+ * cudaMalloc / cudaFree as in te_create).  alloc and free must both be set or
+ * both be NULL (else TE_ERR_INVALID_ARG).  The allocator is copied. */
+te_status te_create_with_allocator(te_ctx** out, int32_t device, void* cuda_stream,
+                                   const te_allocator* allocator);
 void te_destroy(te_ctx* ctx);
 const char* te_last_error(const te_ctx* ctx);
 const char* te_status_string(te_status s);
@@ -457,10 +492,25 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
 /* ---- asynchronous requests --------------------------------------------- */
 
 /* Queue a solve with the same meaning as te_evolve.  v_in is copied before the
- * call returns.  The context's scheduler admits queued requests while their
- * device footprint ((m+1) d 16 bytes plus reduction scratch) fits the
- * context's memory budget and runs admitted requests concurrently, each on its
- * own stream, one restart at a time.  H must outlive the request. */
+ * call returns.  H must outlive the request.  How requests are served
+ * (te_serve_config):
+ *   TE_SERVE_BATCH (default): continuous batching.  One serving loop per
+ *     context keeps the Krylov state of every running request on the device
+ *     in an arena of slots and advances all of them together, one restart of
+ *     Algorithm 1 per round, through the grouped kernels of te_evolve_multi
+ *     (every Lanczos step of all running requests is one launch).  The restart
+ *     boundary is the checkpoint: a queued request is admitted, in arrival
+ *     order, at the next round boundary as soon as a slot of its size
+ *     ((d rounded up to 32) elements of the arena) is free, and a finished
+ *     request leaves at the end of its round.  The result equals te_evolve's
+ *     within the same error bound (the same steps, reductions summed in another
+ *     order).  Requests with reorthogonalisation, the CSR kernel (spmv_lanes),
+ *     TE_OPT_PROFILE, m above the arena depth or d above its capacity go to
+ *     the solo workers instead.
+ *   TE_SERVE_SOLO: up to 8 worker threads each admit the oldest queued request
+ *     once its device footprint ((m+1) d 16 bytes plus reduction scratch)
+ *     fits the context's memory budget, and run it on their own stream, one
+ *     restart graph at a time. */
 te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double t, double tol,
                     int32_t m, const te_options* opt, te_request** out);
 /* TE_PENDING while queued or running; otherwise the solve's status, with the
@@ -477,6 +527,18 @@ void te_request_free(te_request* req);
 /* Bytes of device memory the scheduler may hold for running requests
  * (default: 80% of the free memory at te_create). */
 te_status te_set_memory_budget(te_ctx* ctx, int64_t bytes);
+
+#define TE_SERVE_BATCH 0           /* continuous batching of requests (default) */
+#define TE_SERVE_SOLO  1           /* one solve per worker thread and stream */
+/* How te_submit serves requests.  m_max is the Krylov depth of the serving
+ * arena (1..TE_M_MAX; 0: keep, default 40) and capacity the number of vector
+ * elements per Krylov column it holds (0: keep; default
+ * min(2^24, budget / (16 (m_max + 1) + 8)) at first use).  The arena takes
+ * (m_max + 1) capacity 16 + capacity 8 bytes once the first batched request
+ * arrives, counts against the memory budget, and is released by te_destroy.
+ * Allowed only while no request is queued or running (else
+ * TE_ERR_INVALID_ARG). */
+te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity);
 
 #ifdef __cplusplus
 }

@@ -469,6 +469,7 @@ double now_ms() {
 // ------------------------------------------------------------------ engine
 
 struct BlockPlan {
+    te_ctx* ctx = nullptr;           // owner (device memory through its allocator)
     uint64_t matrix_id = 0;
     int m = 0, B = 0, profile = 0;
     int64_t d = 0;
@@ -496,7 +497,7 @@ void free_block_plan(BlockPlan* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (void* q : {(void*)p->V, (void*)p->S, (void*)p->partials, (void*)p->st, (void*)p->ctr})
-        if (q) cudaFree(q);
+        if (q) dev_free(p->ctx, q);
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->st_init) cudaFreeHost(p->st_init);
     delete p;
@@ -563,14 +564,14 @@ te_status ensure_3m(te_ctx* ctx, const te_matrix* Hc, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_block_mu);
     if (H->m3) return TE_OK;
     double* m3 = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&m3, sizeof(double) * 3 * (size_t)std::max<int64_t>(H->nnz, 1)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &m3, sizeof(double) * 3 * (size_t)std::max<int64_t>(H->nnz, 1)));
     const int64_t want = (H->nnz + TE_BLOCK - 1) / TE_BLOCK;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * 8));
     k_make_3m<<<grid, TE_BLOCK, 0, s>>>(H->val, H->nnz, m3);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFree(m3);
+        dev_free(ctx, m3);
         return cuda_error(ctx, e, "building the 3M form of H");
     }
     H->m3 = m3;
@@ -580,6 +581,7 @@ te_status ensure_3m(te_ctx* ctx, const te_matrix* Hc, cudaStream_t s) {
 te_status create_block_plan(te_ctx* ctx, const te_matrix* H, int m, int B, int profile,
                             cudaStream_t s, BlockPlan** out) {
     BlockPlan* p = new BlockPlan();
+    p->ctx = ctx;
     p->matrix_id = H->id;
     p->m = m;
     p->B = B;
@@ -592,11 +594,11 @@ te_status create_block_plan(te_ctx* ctx, const te_matrix* H, int m, int B, int p
     p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
     const size_t blk = (size_t)H->d * B;
     const size_t npart = (size_t)B * std::max<int64_t>(p->nchunks, p->grid_stream);
-    cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * blk);
-    if (e == cudaSuccess) e = cudaMalloc(&p->S, sizeof(double) * blk);
-    if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * npart);
-    if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState) * B);
-    if (e == cudaSuccess) e = cudaMalloc(&p->ctr, sizeof(unsigned int) * 4);
+    cudaError_t e = dev_alloc(ctx, &p->V, sizeof(double2) * (size_t)(m + 1) * blk);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->S, sizeof(double) * blk);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->partials, sizeof(double) * npart);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->st, sizeof(DevState) * B);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->ctr, sizeof(unsigned int) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState) * B);
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState) * B);
     if (e != cudaSuccess) {

@@ -448,9 +448,13 @@ __global__ void k_row_stats(const int32_t* __restrict__ rowptr, const int32_t* _
 
 template <typename T>
 struct DevBuf {
+    te_ctx* ctx = nullptr;
     T* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-    cudaError_t alloc(size_t n) { return cudaMalloc(&p, n * sizeof(T) + 16); }
+    ~DevBuf() { if (p) dev_free(ctx, p); }
+    cudaError_t alloc(te_ctx* c, size_t n) {
+        ctx = c;
+        return dev_alloc(c, &p, n * sizeof(T) + 16);
+    }
 };
 
 int grid_for(int64_t n) { return (int)((n + TE_BLOCK - 1) / TE_BLOCK); }
@@ -460,9 +464,9 @@ te_status alloc_matrix(te_ctx* ctx, te_matrix* H, int64_t d, int64_t nnz) {
         return set_error(ctx, TE_ERR_UNSUPPORTED, "matrix too large: nnz and d must stay below 2^31");
     H->d = d;
     H->nnz = nnz;
-    if (cudaMalloc(&H->rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess ||
-        cudaMalloc(&H->col, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
-        cudaMalloc(&H->val, sizeof(double2) * (nnz > 0 ? nnz : 1)) != cudaSuccess) {
+    if (dev_alloc(ctx, &H->rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess ||
+        dev_alloc(ctx, &H->col, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        dev_alloc(ctx, &H->val, sizeof(double2) * (nnz > 0 ? nnz : 1)) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
     }
@@ -471,7 +475,7 @@ te_status alloc_matrix(te_ctx* ctx, te_matrix* H, int64_t d, int64_t nnz) {
 
 template <typename T>
 te_status upload(te_ctx* ctx, DevBuf<T>& buf, const T* host, size_t n, cudaStream_t s) {
-    TE_CUDA_TRY(ctx, buf.alloc(n));
+    TE_CUDA_TRY(ctx, buf.alloc(ctx, n));
     TE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.p, host, n * sizeof(T), cudaMemcpyHostToDevice, s));
     return TE_OK;
 }
@@ -499,7 +503,7 @@ te_status scan_counts(te_ctx* ctx, const int32_t* cnt, int64_t d, int32_t* rowpt
                       cudaStream_t s) {
     const int64_t tiles = (d + kScanTile - 1) / kScanTile;
     DevBuf<int64_t> tsum;
-    TE_CUDA_TRY(ctx, tsum.alloc(tiles));
+    TE_CUDA_TRY(ctx, tsum.alloc(ctx, tiles));
     k_scan_tiles<<<(int)tiles, TE_BLOCK, 0, s>>>(cnt, d, tsum.p);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     std::vector<int64_t> h(tiles);
@@ -551,7 +555,7 @@ te_status build_xxzdm(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
     const int64_t d = 1ll << L;
     if (d >= (1ll << 31)) return set_error(ctx, TE_ERR_UNSUPPORTED, "dimension must stay below 2^31");
     DevBuf<int32_t> cnt;
-    TE_CUDA_TRY(ctx, cnt.alloc(d));
+    TE_CUDA_TRY(ctx, cnt.alloc(ctx, d));
     te_status st;
     DevBuf<double> hre, him, hz;
     if ((st = upload(ctx, hre, m->a, nb, s)) || (st = upload(ctx, him, m->b, nb, s)) ||
@@ -560,17 +564,17 @@ te_status build_xxzdm(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
     k_count_xxzdm<<<grid_for(d), TE_BLOCK, 0, s>>>(L, nb, d, cnt.p);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     int32_t* rowptr = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &rowptr, sizeof(int32_t) * (d + 1)));
     int64_t nnz = 0;
     if ((st = scan_counts(ctx, cnt.p, d, rowptr, &nnz, s))) {
-        cudaFree(rowptr);
+        dev_free(ctx, rowptr);
         return st;
     }
     H->d = d;
     H->nnz = nnz;
     H->rowptr = rowptr;
-    if (cudaMalloc(&H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
-        cudaMalloc(&H->val, sizeof(double2) * nnz) != cudaSuccess) {
+    if (dev_alloc(ctx, &H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
+        dev_alloc(ctx, &H->val, sizeof(double2) * nnz) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
     }
@@ -597,10 +601,10 @@ te_status build_bose(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
     DevBuf<unsigned long long> keys;
     DevBuf<int32_t> vals, cnt;
     DevBuf<int> err;
-    TE_CUDA_TRY(ctx, keys.alloc(cap));
-    TE_CUDA_TRY(ctx, vals.alloc(cap));
-    TE_CUDA_TRY(ctx, cnt.alloc(d));
-    TE_CUDA_TRY(ctx, err.alloc(1));
+    TE_CUDA_TRY(ctx, keys.alloc(ctx, cap));
+    TE_CUDA_TRY(ctx, vals.alloc(ctx, cap));
+    TE_CUDA_TRY(ctx, cnt.alloc(ctx, d));
+    TE_CUDA_TRY(ctx, err.alloc(ctx, 1));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(keys.p, 0xff, cap * sizeof(unsigned long long), s));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(err.p, 0, sizeof(int), s));
     const int npair = K * (K - 1) / 2;
@@ -612,17 +616,17 @@ te_status build_bose(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
     k_bose_insert<<<grid_for(d), TE_BLOCK, 0, s>>>(T, d, keys.p, vals.p, cap - 1, cnt.p, err.p);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     int32_t* rowptr = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &rowptr, sizeof(int32_t) * (d + 1)));
     int64_t nnz = 0;
     if ((st = scan_counts(ctx, cnt.p, d, rowptr, &nnz, s))) {
-        cudaFree(rowptr);
+        dev_free(ctx, rowptr);
         return st;
     }
     H->d = d;
     H->nnz = nnz;
     H->rowptr = rowptr;
-    if (cudaMalloc(&H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
-        cudaMalloc(&H->val, sizeof(double2) * nnz) != cudaSuccess) {
+    if (dev_alloc(ctx, &H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
+        dev_alloc(ctx, &H->val, sizeof(double2) * nnz) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
     }
@@ -640,9 +644,9 @@ te_status finish_matrix_stats(te_ctx* ctx, te_matrix* H) {
     cudaStream_t s = ctx->stream;
     DevBuf<unsigned long long> mx;
     DevBuf<int> mn, fl;
-    TE_CUDA_TRY(ctx, mx.alloc(1));
-    TE_CUDA_TRY(ctx, mn.alloc(1));
-    TE_CUDA_TRY(ctx, fl.alloc(1));
+    TE_CUDA_TRY(ctx, mx.alloc(ctx, 1));
+    TE_CUDA_TRY(ctx, mn.alloc(ctx, 1));
+    TE_CUDA_TRY(ctx, fl.alloc(ctx, 1));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(mn.p, 0, sizeof(int), s));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(fl.p, 0, sizeof(int), s));
@@ -701,23 +705,23 @@ te_status build_memory(te_ctx* ctx, const te_model_desc* m, te_matrix* H) {
     DevBuf<int> err;
     te_status st;
     if ((st = upload(ctx, f, m->a, (size_t)std::max(Q * (Q - 1) / 2, 1), s))) return st;
-    TE_CUDA_TRY(ctx, cnt.alloc(d));
-    TE_CUDA_TRY(ctx, err.alloc(1));
+    TE_CUDA_TRY(ctx, cnt.alloc(ctx, d));
+    TE_CUDA_TRY(ctx, err.alloc(ctx, 1));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(err.p, 0, sizeof(int), s));
     k_count_memory<<<grid_for(d), TE_BLOCK, 0, s>>>(T, d, cnt.p);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     int32_t* rowptr = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &rowptr, sizeof(int32_t) * (d + 1)));
     int64_t nnz = 0;
     if ((st = scan_counts(ctx, cnt.p, d, rowptr, &nnz, s))) {
-        cudaFree(rowptr);
+        dev_free(ctx, rowptr);
         return st;
     }
     H->d = d;
     H->nnz = nnz;
     H->rowptr = rowptr;
-    if (cudaMalloc(&H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
-        cudaMalloc(&H->val, sizeof(double2) * nnz) != cudaSuccess) {
+    if (dev_alloc(ctx, &H->col, sizeof(int32_t) * nnz) != cudaSuccess ||
+        dev_alloc(ctx, &H->val, sizeof(double2) * nnz) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
     }
@@ -819,7 +823,7 @@ extern "C" te_status te_model_occupation(te_ctx* ctx, const te_model_desc* desc,
     if (mode < 0 || mode >= modes) return set_error(ctx, TE_ERR_INVALID_ARG, "mode outside the model");
     const bool dev = (flags & TE_PTR_DEVICE) != 0;
     double* dst = out;
-    if (!dev) TE_CUDA_TRY(ctx, cudaMalloc(&dst, sizeof(double) * (size_t)d));
+    if (!dev) TE_CUDA_TRY(ctx, dev_alloc(ctx, &dst, sizeof(double) * (size_t)d));
     const int grid = grid_for(d);
     switch (desc->model) {
         case TE_MODEL_TFIM:
@@ -831,7 +835,7 @@ extern "C" te_status te_model_occupation(te_ctx* ctx, const te_model_desc* desc,
     if (e == cudaSuccess && !dev)
         e = cudaMemcpyAsync(out, dst, sizeof(double) * (size_t)d, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (!dev) cudaFree(dst);
+    if (!dev) dev_free(ctx, dst);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_model_occupation");
     return TE_OK;
 }

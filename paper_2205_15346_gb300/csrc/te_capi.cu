@@ -64,16 +64,17 @@ void free_plan(Plan* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
-    if (p->V) cudaFree(p->V);
-    if (p->S) cudaFree(p->S);
-    if (p->st) cudaFree(p->st);
-    if (p->partials) cudaFree(p->partials);
-    if (p->partials_r) cudaFree(p->partials_r);
-    if (p->bar) cudaFree(p->bar);
+    te_ctx* c = p->ctx;
+    if (p->V) dev_free(c, p->V);
+    if (p->S) dev_free(c, p->S);
+    if (p->st) dev_free(c, p->st);
+    if (p->partials) dev_free(c, p->partials);
+    if (p->partials_r) dev_free(c, p->partials_r);
+    if (p->bar) dev_free(c, p->bar);
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->st_init) cudaFreeHost(p->st_init);
     for (void* q : {(void*)p->samp_ts, (void*)p->samp_coef, (void*)p->samp_buf, (void*)p->samp_bound})
-        if (q) cudaFree(q);
+        if (q) dev_free(c, q);
     delete p;
 }
 
@@ -153,6 +154,7 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
 te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
                       int fused, cudaStream_t s, Plan** out, int ns = 0) {
     Plan* p = new Plan();
+    p->ctx = ctx;
     p->H = H;
     p->fused = fused;
     if (fused && !fused_shape(H, ctx->num_sms, &p->fused_grid, &p->fused_threads)) {
@@ -174,22 +176,22 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
                                                          2 * p->fused_grid),
                                                 lanes ? 0 : sell_partials(H));
     p->bytes = plan_bytes(H->d, m, reorth, max_grid);
-    cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
+    cudaError_t e = dev_alloc(ctx, &p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)H->d);
     // Re + Im of every Krylov column (the sliced SpMV and the recombination read them)
     if (e == cudaSuccess && lanes == 0)
-        e = cudaMalloc(&p->S, sizeof(double) * (size_t)(m + 1) * (size_t)H->d);
-    if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState));
-    if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * (size_t)max_grid);
+        e = dev_alloc(ctx, &p->S, sizeof(double) * (size_t)(m + 1) * (size_t)H->d);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->st, sizeof(DevState));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->partials, sizeof(double) * (size_t)max_grid);
     if (e == cudaSuccess && reorth)
-        e = cudaMalloc(&p->partials_r, sizeof(double) * (size_t)p->grid_reorth * TE_M_MAX * 2);
-    if (e == cudaSuccess && fused) e = cudaMalloc(&p->bar, 4 * sizeof(unsigned int));
+        e = dev_alloc(ctx, &p->partials_r, sizeof(double) * (size_t)p->grid_reorth * TE_M_MAX * 2);
+    if (e == cudaSuccess && fused) e = dev_alloc(ctx, &p->bar, 4 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState));
     if (e == cudaSuccess && ns > 0) {
-        e = cudaMalloc(&p->samp_ts, sizeof(double) * (size_t)ns);
-        if (e == cudaSuccess) e = cudaMalloc(&p->samp_coef, sizeof(double2) * (size_t)ns * m);
-        if (e == cudaSuccess) e = cudaMalloc(&p->samp_buf, sizeof(double2) * (size_t)ns * H->d);
-        if (e == cudaSuccess) e = cudaMalloc(&p->samp_bound, sizeof(double) * (size_t)ns);
+        e = dev_alloc(ctx, &p->samp_ts, sizeof(double) * (size_t)ns);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &p->samp_coef, sizeof(double2) * (size_t)ns * m);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &p->samp_buf, sizeof(double2) * (size_t)ns * H->d);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &p->samp_bound, sizeof(double) * (size_t)ns);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -439,6 +441,29 @@ te_status join_user_stream(te_ctx* ctx) {
 
 // ------------------------------------------------------------------ errors
 
+cudaError_t dev_alloc(te_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (!ctx || !ctx->alloc.alloc) return cudaMalloc(p, bytes);
+    void* q = ctx->alloc.alloc(ctx->alloc.user, bytes, ctx->device, (void*)ctx->stream);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) & 255u) {             // the kernels' vector loads need it
+        ctx->alloc.free(ctx->alloc.user, q, ctx->device, (void*)ctx->stream);
+        return cudaErrorMemoryAllocation;
+    }
+    *p = q;
+    return cudaSuccess;
+}
+
+void dev_free(te_ctx* ctx, void* p) {
+    if (!p) return;
+    if (!ctx || !ctx->alloc.free) {
+        cudaFree(p);
+        return;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    ctx->alloc.free(ctx->alloc.user, p, ctx->device, (void*)ctx->stream);
+}
+
 te_status set_error(te_ctx* ctx, te_status s, const std::string& msg) {
     if (ctx) {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -498,8 +523,14 @@ void te_default_options(te_options* o) {
 const char* te_last_error(const te_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
+    return te_create_with_allocator(out, device, cuda_stream, nullptr);
+}
+
+te_status te_create_with_allocator(te_ctx** out, int32_t device, void* cuda_stream,
+                                   const te_allocator* allocator) {
     if (!out) return TE_ERR_INVALID_ARG;
     *out = nullptr;
+    if (allocator && (!allocator->alloc) != (!allocator->free)) return TE_ERR_INVALID_ARG;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
         cudaGetLastError();
@@ -509,6 +540,7 @@ te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
     if (cudaSetDevice(device) != cudaSuccess) return TE_ERR_CUDA;
     te_ctx* c = new te_ctx();
     c->device = device;
+    if (allocator && allocator->alloc) c->alloc = *allocator;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, device);
     // Work runs on the context's own non-blocking stream (CUDA graphs cannot be
@@ -521,9 +553,9 @@ te_status te_create(te_ctx** out, int32_t device, void* cuda_stream) {
         return TE_ERR_CUDA;
     }
     c->own_stream = true;
-    if (cudaMalloc(&c->spmv_st, sizeof(DevState)) != cudaSuccess ||
+    if (dev_alloc(c, &c->spmv_st, sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&c->spmv_st_host, sizeof(DevState)) != cudaSuccess ||
-        cudaMalloc(&c->spmv_partials, sizeof(double) * (size_t)c->num_sms * 64) != cudaSuccess) {
+        dev_alloc(c, &c->spmv_partials, sizeof(double) * (size_t)c->num_sms * 64) != cudaSuccess) {
         te_destroy(c);
         return TE_ERR_OOM;
     }
@@ -551,13 +583,14 @@ void te_destroy(te_ctx* ctx) {
     ctx->qcv.notify_all();
     for (auto& t : ctx->workers)
         if (t.joinable()) t.join();
+    if (ctx->batcher.joinable()) ctx->batcher.join();
     for (Plan* p : ctx->plans) free_plan(p);
     ctx->plans.clear();
     block_plans_release(ctx, 0);
     multi_plans_release(ctx, 0);
-    if (ctx->spmv_st) cudaFree(ctx->spmv_st);
+    if (ctx->spmv_st) dev_free(ctx, ctx->spmv_st);
     if (ctx->spmv_st_host) cudaFreeHost(ctx->spmv_st_host);
-    if (ctx->spmv_partials) cudaFree(ctx->spmv_partials);
+    if (ctx->spmv_partials) dev_free(ctx, ctx->spmv_partials);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->user_ev) cudaEventDestroy(ctx->user_ev);
     delete ctx;
@@ -656,9 +689,9 @@ te_status te_build_csr(te_ctx* ctx, int64_t d, int64_t n_entries, const int64_t*
     H->ctx = ctx;
     H->d = d;
     H->nnz = nnz;
-    if (cudaMalloc(&H->rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess ||
-        cudaMalloc(&H->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
-        cudaMalloc(&H->val, sizeof(double2) * std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+    if (dev_alloc(ctx, &H->rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess ||
+        dev_alloc(ctx, &H->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+        dev_alloc(ctx, &H->val, sizeof(double2) * std::max<int64_t>(nnz, 1)) != cudaSuccess) {
         cudaGetLastError();
         te_matrix_free(H);
         return set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed");
@@ -776,7 +809,7 @@ void te_matrix_free(te_matrix* H) {
                     (void*)H->iperm, (void*)H->sell_off, (void*)H->sell_col, (void*)H->sell_a, (void*)H->sell_pq,
                     (void*)H->sell_idx, (void*)H->sell_diag, (void*)H->dict_a, (void*)H->dict_pq,
                     (void*)H->m3})
-        if (q) cudaFree(q);
+        if (q) dev_free(ctx, q);
     delete H;
 }
 
@@ -812,7 +845,7 @@ te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* bes
     H->sell_tpt = keep;
     double2* x = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&x, sizeof(double2) * 2 * (size_t)d + sizeof(double) * ((size_t)d + np));
+    cudaError_t e = dev_alloc(ctx, &x, sizeof(double2) * 2 * (size_t)d + sizeof(double) * ((size_t)d + np));
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_matrix_tune scratch");
     double2* y = x + d;
     double* xsum = reinterpret_cast<double*>(y + d);
@@ -844,7 +877,7 @@ te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* bes
     H->sell_tpt = (e == cudaSuccess) ? best_tpt : keep;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(x);
+    dev_free(ctx, x);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_matrix_tune");
     if (best_ms) *best_ms = best;
     return TE_OK;
@@ -864,7 +897,7 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
     // the product runs in the length-sorted basis of the SELL form: x enters
     // through perm, y leaves through iperm
     double2 *xs = nullptr, *ys = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&xs, sizeof(double2) * 2 * (size_t)d + sizeof(double) * (size_t)d +
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &xs, sizeof(double2) * 2 * (size_t)d + sizeof(double) * (size_t)d +
                                          sizeof(double) * (size_t)sell_partials(H)));
     ys = xs + d;
     double* xsum = reinterpret_cast<double*>(ys + d);
@@ -891,7 +924,7 @@ te_status te_spmv(te_ctx* ctx, const te_matrix* H, const double* x, double* y, d
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->spmv_st_host, ctx->spmv_st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(xs);
+    dev_free(ctx, xs);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_spmv");
     if (x_dot_y) *x_dot_y = ctx->spmv_st_host->spmv_dot;
     return TE_OK;
@@ -986,7 +1019,7 @@ te_status te_evolve_sampled(te_ctx* ctx, const te_matrix* H, const double* v_in,
     if (e == cudaSuccess && n_obs > 0) {
         const int G = ctx->num_sms;
         double *Op = nullptr, *part = nullptr, *res = nullptr;
-        e = cudaMalloc(&Op, sizeof(double) * ((size_t)n_obs * d + (size_t)n_samples * n_obs * G +
+        e = dev_alloc(ctx, &Op, sizeof(double) * ((size_t)n_obs * d + (size_t)n_samples * n_obs * G +
                                               (size_t)n_samples * n_obs));
         if (e == cudaSuccess) {
             part = Op + (size_t)n_obs * d;
@@ -1008,7 +1041,7 @@ te_status te_evolve_sampled(te_ctx* ctx, const te_matrix* H, const double* v_in,
                 e = cudaMemcpyAsync(obs_out, res, sizeof(double) * (size_t)n_samples * n_obs,
                                     cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            cudaFree(Op);
+            dev_free(ctx, Op);
         }
     }
     if (e == cudaSuccess && sample_bounds)
@@ -1093,6 +1126,22 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
 
 // ------------------------------------------------------------------ requests
 
+te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity) {
+    if (!ctx || (mode != TE_SERVE_BATCH && mode != TE_SERVE_SOLO) || m_max < 0 || m_max > TE_M_MAX ||
+        capacity < 0)
+        return TE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->qmu);
+    if (ctx->pending != 0)
+        return set_error(ctx, TE_ERR_INVALID_ARG, "te_serve_config: requests are queued or running");
+    if (ctx->batcher.joinable() && (m_max != 0 || capacity != 0))
+        return set_error(ctx, TE_ERR_INVALID_ARG,
+                         "te_serve_config: the serving arena exists; set its shape before the first request");
+    ctx->serve_mode = mode;
+    if (m_max) ctx->serve_m = m_max;
+    if (capacity) ctx->serve_cap = std::max<int64_t>(32, capacity / 32 * 32);
+    return TE_OK;
+}
+
 te_status te_set_memory_budget(te_ctx* ctx, int64_t bytes) {
     if (!ctx || bytes <= 0) return TE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->qmu);
@@ -1120,7 +1169,7 @@ te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
     r->m = (int32_t)std::min<int64_t>(m, H->d);
     r->opt = o;
     const size_t vb = sizeof(double2) * (size_t)H->d;
-    if (cudaMalloc(&r->v_in_dev, vb) != cudaSuccess || cudaMalloc(&r->v_out_dev, vb) != cudaSuccess) {
+    if (dev_alloc(ctx, &r->v_in_dev, vb) != cudaSuccess || dev_alloc(ctx, &r->v_out_dev, vb) != cudaSuccess) {
         cudaGetLastError();
         te_request_free(r);
         return set_error(ctx, TE_ERR_OOM, "request vectors");
@@ -1134,8 +1183,18 @@ te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
     r->footprint = plan_bytes(H->d, r->m, o.reorth, ctx->num_sms * 8);
     {
         std::lock_guard<std::mutex> lk(ctx->qmu);
-        ctx->queue.push_back(r);
-        if ((int)ctx->workers.size() < ctx->max_workers) ctx->workers.emplace_back(worker_loop, ctx);
+        if (ctx->serve_mode == TE_SERVE_BATCH && ctx->serve_cap == 0) {
+            const int64_t per = 16 * (int64_t)(ctx->serve_m + 1) + 8;
+            ctx->serve_cap = std::max<int64_t>(32, std::min<int64_t>(1ll << 24, ctx->budget / per) / 32 * 32);
+        }
+        ctx->pending += 1;
+        if (serve_eligible(ctx, r)) {
+            ctx->bqueue.push_back(r);
+            if (!ctx->batcher.joinable()) ctx->batcher = std::thread(serve_loop, ctx);
+        } else {
+            ctx->queue.push_back(r);
+            if ((int)ctx->workers.size() < ctx->max_workers) ctx->workers.emplace_back(worker_loop, ctx);
+        }
     }
     ctx->qcv.notify_all();
     *out = r;
@@ -1180,10 +1239,13 @@ void te_request_free(te_request* r) {
     bool queued_removed = false;
     if (ctx) {
         std::lock_guard<std::mutex> lk(ctx->qmu);
-        auto it = std::find(ctx->queue.begin(), ctx->queue.end(), r);
-        if (it != ctx->queue.end()) {
-            ctx->queue.erase(it);
-            queued_removed = true;
+        for (auto* q : {&ctx->queue, &ctx->bqueue}) {
+            auto it = std::find(q->begin(), q->end(), r);
+            if (it != q->end()) {
+                q->erase(it);
+                queued_removed = true;
+                ctx->pending -= 1;
+            }
         }
     }
     if (!queued_removed && r->state.load() == 1) {
@@ -1191,8 +1253,8 @@ void te_request_free(te_request* r) {
         r->cv.wait(lk, [&] { return r->state.load() == 2; });
     }
     if (ctx) cudaSetDevice(ctx->device);
-    if (r->v_in_dev) cudaFree(r->v_in_dev);
-    if (r->v_out_dev) cudaFree(r->v_out_dev);
+    if (r->v_in_dev) dev_free(r->ctx, r->v_in_dev);
+    if (r->v_out_dev) dev_free(r->ctx, r->v_out_dev);
     delete r;
 }
 
@@ -1209,6 +1271,7 @@ void worker_loop(te_ctx* ctx) {
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (;;) {
         te_request* r = nullptr;
+        bool counted = false;                 // r's footprint is in ctx->in_use
         {
             std::unique_lock<std::mutex> lk(ctx->qmu);
             ctx->qcv.wait(lk, [&] {
@@ -1226,6 +1289,7 @@ void worker_loop(te_ctx* ctx) {
                 r = ctx->queue.front();
                 ctx->queue.pop_front();
                 ctx->in_use += (int64_t)r->footprint;
+                counted = true;
             }
             r->state.store(1);
         }
@@ -1251,8 +1315,11 @@ void worker_loop(te_ctx* ctx) {
                 std::lock_guard<std::mutex> lk(ctx->mu);
                 msg = ctx->err;
             }
+        }
+        {
             std::lock_guard<std::mutex> lk(ctx->qmu);
-            ctx->in_use -= (int64_t)r->footprint;
+            if (counted) ctx->in_use -= (int64_t)r->footprint;
+            ctx->pending -= 1;
         }
         ctx->qcv.notify_all();
         {

@@ -333,7 +333,7 @@ extern "C" te_status te_fused_barrier_check(te_ctx* ctx, int32_t absent_block, i
     TE_CUDA_TRY(ctx, cudaEventRecord(ctx->user_ev, ctx->user_stream));
     TE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->user_ev, 0));
     unsigned int* bar = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&bar, 4 * sizeof(unsigned int)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &bar, 4 * sizeof(unsigned int)));
     int* cnt = reinterpret_cast<int*>(bar + 3);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned int), s);
@@ -360,7 +360,7 @@ extern "C" te_status te_fused_barrier_check(te_ctx* ctx, int32_t absent_block, i
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(bar);
+    dev_free(ctx, bar);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_fused_barrier_check");
     *passed = h;
     if (ms) *ms = t;

@@ -126,6 +126,7 @@ struct te_matrix {
 
 // One solve's device workspace and captured restart graph.
 struct Plan {
+    te_ctx* ctx = nullptr;           // owner: its allocator holds the device memory below
     const te_matrix* H = nullptr;
     // intermediate-time sampling (te_sample.cu); such plans are built per call
     int ns = 0;                      // sample times
@@ -180,6 +181,7 @@ struct te_request {
 
 struct te_ctx {
     int device = 0;
+    te_allocator alloc{};            // caller's device allocator (alloc == NULL: cudaMalloc)
     cudaStream_t stream = nullptr;        // the context's own non-blocking stream
     cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy default)
     cudaEvent_t user_ev = nullptr;
@@ -197,13 +199,23 @@ struct te_ctx {
     // scheduler
     std::mutex qmu;
     std::condition_variable qcv;
-    std::deque<te_request*> queue;
+    std::deque<te_request*> queue;   // requests for the solo workers
     std::vector<std::thread> workers;
+    std::deque<te_request*> bqueue;  // requests for the serving loop (continuous batching)
+    std::thread batcher;
+    int serve_mode = TE_SERVE_BATCH;
+    int serve_m = 40;                // Krylov depth of the serving arena
+    int64_t serve_cap = 0;           // elements per arena column (0: from the budget at first use)
+    int64_t pending = 0;             // requests submitted and not yet finished
     bool stopping = false;
     int64_t budget = 0;
     int64_t in_use = 0;
     int max_workers = 8;
 };
+
+// continuous-batching serving loop (te_multi.cu)
+bool serve_eligible(const te_ctx* ctx, const te_request* r);
+void serve_loop(te_ctx* ctx);
 
 // ---- host launchers (kernels live in te_lanczos.cu, te_step.cu, te_build.cu)
 
@@ -286,6 +298,16 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
 void gauss_legendre_table(int n, double* x, double* w);
 
 te_status set_error(te_ctx* ctx, te_status s, const std::string& msg);
+
+// Device memory of a context: the caller's allocator (te_create_with_allocator),
+// else cudaMalloc / cudaFree.  dev_free first waits for the context's stream, so
+// a caller's pool may hand the memory out again at once.
+cudaError_t dev_alloc(te_ctx* ctx, void** p, size_t bytes);
+void dev_free(te_ctx* ctx, void* p);
+template <class T>
+inline cudaError_t dev_alloc(te_ctx* ctx, T** p, size_t bytes) {
+    return dev_alloc(ctx, reinterpret_cast<void**>(p), bytes);
+}
 // Device status TE_ERR_UNSUPPORTED from the step or sample kernel: exp(-i H_m tau) e_1
 // after a lucky breakdown needed more series pieces than the build allows.
 constexpr const char* kSeriesRangeMsg =

@@ -92,6 +92,13 @@ __device__ __forceinline__ int owner(const int64_t* start, int n, int64_t c) {
     return lo;
 }
 
+// The initial normalisation (init mode of KM0 / beta0) is for problems that have
+// not started: a problem that already took a restart (a request carried over
+// into a new group by the serving loop) keeps its vector and scale.
+__device__ __forceinline__ bool fresh_skip(const DevState* s) {
+    return s->done != 0 || s->restarts != 0;
+}
+
 // A problem takes part in Lanczos step j while it runs and j is inside its
 // Krylov dimension (m_p = min(m, d_p)).
 __device__ __forceinline__ bool step_idle(const DevState* s, int j) {
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(TE_BLOCK) k_recombine_multi(
     for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
         const int p = owner(cs, n, g);
         const DevState* sp = st + p;
-        if (init ? sp->done != 0 : (sp->active == 0 || sp->status != 0)) continue;
+        if (init ? fresh_skip(sp) : (sp->active == 0 || sp->status != 0)) continue;
         const int nk = init ? 0 : sp->last_m_eff;
         __syncthreads();                                // c[] of the previous chunk is consumed
         for (int k = threadIdx.x; k < nk; k += blockDim.x) c[k] = sp->coef[k];
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_beta0_multi(DevState* st, co
                                                           const double* partials, int init) {
     __shared__ double sh[32];
     DevState* sp = st + blockIdx.x;
-    if (init ? sp->done != 0 : (sp->active == 0 || sp->status != 0)) return;
+    if (init ? fresh_skip(sp) : (sp->active == 0 || sp->status != 0)) return;
     const int64_t c0 = chunk_start[blockIdx.x];
     const double nrm = sqrt(sum_range(partials + c0, chunk_start[blockIdx.x + 1] - c0, sh));
     if (threadIdx.x == 0) {
@@ -339,6 +346,56 @@ __global__ void __launch_bounds__(kReduceThreads) k_beta0_multi(DevState* st, co
         else if (init && fabs(nrm - 1.0) > 1e-10) sp->status = TE_ERR_NOT_NORMALIZED;
         if (init && sp->T == 0.0) sp->done = 1;       // t = 0: validated, nothing to evolve
     }
+}
+
+// The state of a problem before its first restart (constants of the solve).
+void initial_state(DevState* x, double t, double tol, int m, const te_options& o) {
+    memset(x, 0, sizeof(DevState));
+    double gx[TE_GAUSS_MAX], gw[TE_GAUSS_MAX];
+    gauss_legendre_table(o.gauss_n, gx, gw);
+    x->T = fabs(t);
+    x->tol_rate = (t != 0.0) ? tol / fabs(t) : tol;      // eq. errorRate
+    x->sign = (t >= 0.0) ? 1.0 : -1.0;
+    x->t_step0 = o.t_step0;
+    x->shrink = o.shrink;
+    x->quad_rel_tol = o.quad_rel_tol;
+    x->min_step = o.min_step_rel * fabs(t);
+    x->m = m;
+    x->n_substeps = o.n_substeps;
+    x->quad = o.quad;
+    x->gauss_n = o.gauss_n;
+    x->quad_max_levels = o.quad_max_levels;
+    x->max_substeps = o.max_substeps;
+    x->smallexp = o.small_exp;
+    x->first = 1;
+    x->m_eff = m;
+    x->min_err_step = INFINITY;
+    memcpy(x->gx, gx, sizeof(gx));
+    memcpy(x->gw, gw, sizeof(gw));
+}
+
+// te_stats of a finished problem from its device state.
+te_stats stats_from_state(const DevState& x, const te_matrix* H, double t) {
+    const double per_restart = (double)H->d * H->norm1 * 2.220446049250313e-16;
+    te_stats S;
+    memset(&S, 0, sizeof(S));
+    S.norm_in = x.beta0;
+    S.m_used = x.m;
+    S.restarts = x.restarts;
+    S.matvecs = x.matvecs;
+    S.breakdowns = x.breakdowns;
+    S.quad_warnings = x.quad_warnings;
+    S.quad_integrals = x.quad_integrals;
+    S.quad_nodes = x.quad_nodes;
+    S.eig_mcycles = 1e-6 * (double)x.eig_cycles;
+    S.search_mcycles = 1e-6 * (double)x.search_cycles;
+    S.err_bound = x.err_acc;
+    S.roundoff_est = per_restart * (double)x.restarts;
+    if (x.restarts > 0 && per_restart > x.min_err_step) S.flags |= TE_WARN_ROUNDOFF;
+    if (x.breakdowns) S.flags |= TE_FLAG_BREAKDOWN;
+    if (x.quad_warnings) S.flags |= TE_WARN_QUAD;
+    S.t_reached = (t == 0.0) ? 0.0 : (t >= 0.0 ? 1.0 : -1.0) * x.t_now;
+    return S;
 }
 
 double now_ms() {
@@ -384,7 +441,7 @@ void free_multi_plan(MultiPlan* p) {
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (void* q : {(void*)p->V, (void*)p->S, (void*)p->partials, (void*)p->st, (void*)p->probs,
                     (void*)p->task_start, (void*)p->chunk_start, (void*)p->ctr})
-        if (q) cudaFree(q);
+        if (q) dev_free(p->ctx, q);
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->st_init) cudaFreeHost(p->st_init);
     delete p;
@@ -477,14 +534,14 @@ te_status create_multi_plan(te_ctx* ctx, int n, const te_matrix* const* H, int m
                                                                 (int64_t)std::max(occ, 1) * ctx->num_sms));
     p->grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>(p->nchunks, (int64_t)ctx->num_sms * 8));
     const size_t npart = (size_t)std::max(p->ntasks, p->nchunks);
-    cudaError_t e = cudaMalloc(&p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)p->dsum);
-    if (e == cudaSuccess) e = cudaMalloc(&p->S, sizeof(double) * (size_t)p->dsum);
-    if (e == cudaSuccess) e = cudaMalloc(&p->partials, sizeof(double) * npart);
-    if (e == cudaSuccess) e = cudaMalloc(&p->st, sizeof(DevState) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&p->probs, sizeof(MProb) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&p->task_start, sizeof(int64_t) * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p->chunk_start, sizeof(int64_t) * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p->ctr, sizeof(unsigned int) * 4);
+    cudaError_t e = dev_alloc(ctx, &p->V, sizeof(double2) * (size_t)(m + 1) * (size_t)p->dsum);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->S, sizeof(double) * (size_t)p->dsum);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->partials, sizeof(double) * npart);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->st, sizeof(DevState) * n);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->probs, sizeof(MProb) * n);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->task_start, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->chunk_start, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &p->ctr, sizeof(unsigned int) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_host, sizeof(DevState) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&p->st_init, sizeof(DevState) * n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->probs, hp.data(), sizeof(MProb) * n, cudaMemcpyHostToDevice, s);
@@ -600,32 +657,8 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
         return cuda_error(ctx, e, what);
     };
     DevState* ini = p->st_init;
-    memset(ini, 0, sizeof(DevState) * n);
-    double gx[TE_GAUSS_MAX], gw[TE_GAUSS_MAX];
-    gauss_legendre_table(o.gauss_n, gx, gw);
-    for (int i = 0; i < n; ++i) {
-        DevState& x = ini[i];
-        const double ti = t[i];
-        x.T = fabs(ti);
-        x.tol_rate = (ti != 0.0) ? tol / fabs(ti) : tol;
-        x.sign = (ti >= 0.0) ? 1.0 : -1.0;
-        x.t_step0 = o.t_step0;
-        x.shrink = o.shrink;
-        x.quad_rel_tol = o.quad_rel_tol;
-        x.min_step = o.min_step_rel * fabs(ti);
-        x.m = (int)std::min<int64_t>(m, H[i]->d);
-        x.n_substeps = o.n_substeps;
-        x.quad = o.quad;
-        x.gauss_n = o.gauss_n;
-        x.quad_max_levels = o.quad_max_levels;
-        x.max_substeps = o.max_substeps;
-        x.smallexp = o.small_exp;
-        x.first = 1;
-        x.m_eff = x.m;
-        x.min_err_step = INFINITY;
-        memcpy(x.gx, gx, sizeof(gx));
-        memcpy(x.gw, gw, sizeof(gw));
-    }
+    for (int i = 0; i < n; ++i)
+        initial_state(&ini[i], t[i], tol, (int)std::min<int64_t>(m, H[i]->d), o);
     const int64_t blk = p->dsum;
     double2* stage = p->V + (size_t)m * (size_t)blk;   // the last block is free outside a round
     cudaError_t e = cudaMemcpyAsync(p->st, ini, sizeof(DevState) * n, cudaMemcpyHostToDevice, s);
@@ -696,25 +729,7 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
         if (status) status[i] = si;
         if (si != TE_OK && worst == TE_OK) worst = si;
         if (!stats) continue;
-        const double per_restart = (double)H[i]->d * H[i]->norm1 * 2.220446049250313e-16;
-        te_stats S;
-        memset(&S, 0, sizeof(S));
-        S.norm_in = x.beta0;
-        S.m_used = x.m;
-        S.restarts = x.restarts;
-        S.matvecs = x.matvecs;
-        S.breakdowns = x.breakdowns;
-        S.quad_warnings = x.quad_warnings;
-        S.quad_integrals = x.quad_integrals;
-        S.quad_nodes = x.quad_nodes;
-        S.eig_mcycles = 1e-6 * (double)x.eig_cycles;
-        S.search_mcycles = 1e-6 * (double)x.search_cycles;
-        S.err_bound = x.err_acc;
-        S.roundoff_est = per_restart * (double)x.restarts;
-        if (x.restarts > 0 && per_restart > x.min_err_step) S.flags |= TE_WARN_ROUNDOFF;
-        if (x.breakdowns) S.flags |= TE_FLAG_BREAKDOWN;
-        if (x.quad_warnings) S.flags |= TE_WARN_QUAD;
-        S.t_reached = (t[i] == 0.0) ? 0.0 : (t[i] >= 0.0 ? 1.0 : -1.0) * x.t_now;
+        te_stats S = stats_from_state(x, H[i], t[i]);
         S.spmv_ms = spmv_ms;
         S.spmv_launches = spmv_launches;
         S.solve_ms = el;
@@ -733,4 +748,392 @@ te_status run_multi_solve(te_ctx* ctx, int n, const te_matrix* const* H, const d
     release();
     (void)rounds;
     return worst;
+}
+
+// ------------------------------------------------------------------ continuous batching
+//
+// The serving loop behind te_submit.  Algorithm 1's restart boundary (a state is
+// fully described by the vector w and a few scalars once step 3 has formed w) is
+// the checkpoint at which requests join and leave: every running request takes
+// part in each round (one restart of all of them through the grouped kernels of
+// this file, one captured graph per composition), a queued request is admitted
+// at the next round boundary as soon as a slot of the Krylov arena is free, and
+// a finished request leaves at the end of its round.  The arena holds the
+// (m_max + 1) Krylov columns of every slot at a fixed column stride, so a
+// request keeps its place while others come and go; admission by HBM footprint
+// is admission by free arena space.
+
+namespace {
+
+struct ServeSlot {
+    te_request* r = nullptr;
+    int64_t elem0 = 0, seg = 0;     // arena segment
+    int idx = -1;                   // position in the captured composition (-1: new)
+    double t_admit = 0.0;
+};
+
+struct ServeEngine {
+    te_ctx* ctx = nullptr;
+    cudaStream_t s = nullptr;
+    int depth = 0;                  // Krylov dimension of the arena
+    int64_t cap = 0;                // elements per Krylov column
+    size_t npart = 0;
+    size_t bytes = 0;
+    double2* V = nullptr;
+    double* S = nullptr;
+    double* partials = nullptr;
+    DevState* st = nullptr;
+    DevState* st_host = nullptr;
+    DevState* st_init = nullptr;
+    MProb* probs = nullptr;
+    int64_t* task_start = nullptr;
+    int64_t* chunk_start = nullptr;
+    unsigned int* ctr = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ServeSlot> slots;   // running requests, in composition order
+    std::vector<std::pair<int64_t, int64_t>> holes;   // free arena segments (offset, length)
+    bool dirty = true;              // composition changed since the last capture
+
+    te_status init(te_ctx* c, int m_max, int64_t capacity) {
+        ctx = c;
+        depth = m_max;
+        cap = capacity / 32 * 32;
+        npart = (size_t)(cap / 32 + 2 * TE_MULTI_MAX + 1);
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &V, sizeof(double2) * (size_t)(depth + 1) * (size_t)cap);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &S, sizeof(double) * (size_t)cap);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &partials, sizeof(double) * npart);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &st, sizeof(DevState) * TE_MULTI_MAX);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &probs, sizeof(MProb) * TE_MULTI_MAX);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &task_start, sizeof(int64_t) * (TE_MULTI_MAX + 1));
+        if (e == cudaSuccess) e = dev_alloc(ctx, &chunk_start, sizeof(int64_t) * (TE_MULTI_MAX + 1));
+        if (e == cudaSuccess) e = dev_alloc(ctx, &ctr, sizeof(unsigned int) * 4);
+        if (e == cudaSuccess) e = cudaMallocHost(&st_host, sizeof(DevState) * TE_MULTI_MAX);
+        if (e == cudaSuccess) e = cudaMallocHost(&st_init, sizeof(DevState) * TE_MULTI_MAX);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int) * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, sizeof(double) * (size_t)cap, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, e == cudaErrorMemoryAllocation ? TE_ERR_OOM : TE_ERR_CUDA,
+                             std::string("allocating the serving arena: ") + cudaGetErrorString(e));
+        }
+        bytes = sizeof(double2) * (size_t)(depth + 1) * (size_t)cap + sizeof(double) * ((size_t)cap + npart);
+        holes.push_back({0, cap});
+        return TE_OK;
+    }
+
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        for (void* q : {(void*)V, (void*)S, (void*)partials, (void*)st, (void*)probs,
+                        (void*)task_start, (void*)chunk_start, (void*)ctr})
+            if (q) dev_free(ctx, q);
+        if (st_host) cudaFreeHost(st_host);
+        if (st_init) cudaFreeHost(st_init);
+        if (s) cudaStreamDestroy(s);
+        V = nullptr;
+        S = nullptr;
+        st_host = st_init = nullptr;
+        s = nullptr;
+    }
+
+    // first-fit arena segment of `len` elements (-1: none)
+    int64_t take(int64_t len) {
+        for (size_t i = 0; i < holes.size(); ++i) {
+            if (holes[i].second < len) continue;
+            const int64_t off = holes[i].first;
+            holes[i].first += len;
+            holes[i].second -= len;
+            if (holes[i].second == 0) holes.erase(holes.begin() + (long)i);
+            return off;
+        }
+        return -1;
+    }
+
+    void give(int64_t off, int64_t len) {
+        holes.push_back({off, len});
+        std::sort(holes.begin(), holes.end());
+        std::vector<std::pair<int64_t, int64_t>> merged;
+        for (auto& h : holes) {
+            if (!merged.empty() && merged.back().first + merged.back().second == h.first)
+                merged.back().second += h.second;
+            else
+                merged.push_back(h);
+        }
+        holes.swap(merged);
+    }
+};
+
+// Tables, states and graph of the current composition; new slots are started
+// (vector gathered into the arena in the matrix's sorted basis, normalisation
+// checked).  Carried slots keep their arena columns and continue from their
+// state of the last round.
+te_status serve_compose(ServeEngine& E) {
+    te_ctx* ctx = E.ctx;
+    const int n = (int)E.slots.size();
+    std::vector<MProb> hp(n);
+    std::vector<int64_t> ts(n + 1, 0), cs(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const te_matrix* A = E.slots[i].r->H;
+        MProb& q = hp[i];
+        memset(&q, 0, sizeof(q));
+        q.off = A->sell_off;
+        q.col = A->sell_col;
+        q.vidx = A->sell_idx;
+        q.ta = A->dict_a;
+        q.tpq = A->dict_pq;
+        q.diag = A->sell_diag;
+        q.va = A->sell_a;
+        q.vpq = A->sell_pq;
+        q.d = A->d;
+        q.nslices = A->nslices;
+        q.tpt = A->sell_tpt;
+        q.real = A->dict_real ? 1 : 0;
+        q.elem0 = E.slots[i].elem0;
+        ts[i + 1] = ts[i] + (A->nslices + A->sell_tpt - 1) / A->sell_tpt;
+        cs[i + 1] = cs[i] + (A->d + kChunkElems - 1) / kChunkElems;
+        const ServeSlot& sl = E.slots[i];
+        if (sl.idx >= 0) {
+            E.st_init[i] = E.st_host[sl.idx];
+        } else {
+            const te_request* r = sl.r;
+            initial_state(&E.st_init[i], r->t, r->tol, r->m, r->opt);
+        }
+    }
+    cudaStream_t s = E.s;
+    cudaError_t e = cudaMemcpyAsync(E.probs, hp.data(), sizeof(MProb) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E.task_start, ts.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E.chunk_start, cs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E.st, E.st_init, sizeof(DevState) * n, cudaMemcpyHostToDevice, s);
+    bool fresh = false;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        ServeSlot& sl = E.slots[i];
+        if (sl.idx >= 0) continue;
+        fresh = true;
+        e = launch_gather((const double2*)sl.r->v_in_dev, sl.r->H->perm, sl.r->H->d, E.V + sl.elem0,
+                          E.S + sl.elem0, ctx->num_sms, s);
+    }
+    int grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>(cs[n], (int64_t)ctx->num_sms * 8));
+    if (e == cudaSuccess && fresh) {
+        k_recombine_multi<<<grid_stream, TE_BLOCK, 0, s>>>(E.probs, E.chunk_start, n, E.V, E.S, E.cap,
+                                                           E.st, 1, E.partials);
+        k_beta0_multi<<<n, kReduceThreads, 0, s>>>(E.st, E.chunk_start, E.partials, 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E.st_host, E.st, sizeof(DevState) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "starting a serving round");
+    for (int i = 0; i < n; ++i) E.slots[i].idx = i;
+    // the round graph of this composition
+    if (E.exec) cudaGraphExecDestroy(E.exec);
+    E.exec = nullptr;
+    MultiPlan mp;
+    mp.ctx = ctx;
+    mp.m = E.depth;
+    mp.n = n;
+    mp.dsum = E.cap;
+    mp.ntasks = ts[n];
+    mp.nchunks = cs[n];
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_multi, TE_BLOCK, 0);
+    mp.grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>((mp.ntasks + 7) / 8,
+                                                                (int64_t)std::max(occ, 1) * ctx->num_sms));
+    mp.grid_stream = grid_stream;
+    mp.V = E.V;
+    mp.S = E.S;
+    mp.partials = E.partials;
+    mp.st = E.st;
+    mp.st_host = E.st_host;
+    mp.probs = E.probs;
+    mp.task_start = E.task_start;
+    mp.chunk_start = E.chunk_start;
+    mp.ctr = E.ctr;
+    te_status cst = capture_multi_round(ctx, &mp, s);
+    E.exec = mp.exec;
+    mp.exec = nullptr;
+    E.dirty = false;
+    return cst;
+}
+
+// Publish a request's outcome (the vector is already in r->v_out_dev when ok).
+void serve_publish(te_request* r, te_status res, const te_stats& S, const std::string& msg) {
+    {
+        std::lock_guard<std::mutex> lk(r->ctx->qmu);
+        r->ctx->pending -= 1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(r->mu);
+        r->stats = S;
+        r->result = res;
+        r->err = msg;
+        r->state.store(2);
+    }
+    r->cv.notify_all();
+}
+
+// Finished or failed slot i: its result leaves the arena (back to the caller's
+// basis) and the slot is released.
+void serve_finish(ServeEngine& E, size_t i, te_status res, const std::string& msg) {
+    ServeSlot sl = E.slots[i];
+    te_request* r = sl.r;
+    te_stats S;
+    memset(&S, 0, sizeof(S));
+    if (sl.idx >= 0) S = stats_from_state(E.st_host[sl.idx], r->H, r->t);
+    if (res == TE_OK || res == TE_ERR_STEP_UNDERFLOW) {
+        cudaError_t e = launch_gather(E.V + sl.elem0, r->H->iperm, r->H->d, (double2*)r->v_out_dev,
+                                      nullptr, E.ctx->num_sms, E.s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E.s);
+        if (e != cudaSuccess) {
+            res = TE_ERR_CUDA;
+            cudaGetLastError();
+        }
+    }
+    S.solve_ms = now_ms() - sl.t_admit;
+    E.slots.erase(E.slots.begin() + (long)i);
+    E.give(sl.elem0, sl.seg);
+    E.dirty = true;
+    serve_publish(r, res, S, msg);
+}
+
+const char* device_status_msg(te_status s) {
+    switch (s) {
+        case TE_ERR_NOT_NORMALIZED: return "the request vector is not normalised (| ||v|| - 1 | > 1e-10)";
+        case TE_ERR_NONFINITE: return "non-finite values in the request";
+        case TE_ERR_STEP_UNDERFLOW: return "step size underflow: no step meets the error rate";
+        case TE_ERR_UNSUPPORTED: return kSeriesRangeMsg;
+        default: return "the request failed on the device";
+    }
+}
+
+}  // namespace
+
+bool serve_eligible(const te_ctx* ctx, const te_request* r) {
+    return ctx->serve_mode == TE_SERVE_BATCH && r->opt.reorth == TE_REORTH_NONE &&
+           r->opt.spmv_lanes == 0 && !(r->opt.flags & TE_OPT_PROFILE) && r->m <= ctx->serve_m &&
+           r->H->sell_off != nullptr && (r->H->d + 31) / 32 * 32 <= ctx->serve_cap;
+}
+
+// The serving loop (one thread per context, started by the first batched request).
+void serve_loop(te_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    ServeEngine E;
+    te_status init_st = TE_OK;
+    bool ready = false;
+    for (;;) {
+        std::vector<te_request*> cancelled;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->qcv.wait(lk, [&] { return ctx->stopping || !ctx->bqueue.empty() || !E.slots.empty(); });
+            if (ctx->stopping) {
+                for (te_request* r : ctx->bqueue) {
+                    r->state.store(1);
+                    cancelled.push_back(r);
+                }
+                ctx->bqueue.clear();
+            } else {
+                if (!ready && init_st == TE_OK) {
+                    lk.unlock();
+                    init_st = E.init(ctx, ctx->serve_m, ctx->serve_cap);
+                    lk.lock();
+                    if (init_st == TE_OK) {
+                        ready = true;
+                        ctx->in_use += (int64_t)E.bytes;
+                    }
+                }
+                if (!ready) {                           // no arena: every queued request fails
+                    for (te_request* r : ctx->bqueue) {
+                        r->state.store(1);
+                        cancelled.push_back(r);
+                    }
+                    ctx->bqueue.clear();
+                }
+                // admission in arrival order while slots and arena space last
+                while (ready && !ctx->bqueue.empty() && (int)E.slots.size() < TE_MULTI_MAX) {
+                    te_request* r = ctx->bqueue.front();
+                    if (r->cancel.load()) {
+                        ctx->bqueue.pop_front();
+                        r->state.store(1);
+                        cancelled.push_back(r);
+                        continue;
+                    }
+                    const int64_t seg = (r->H->d + 31) / 32 * 32;
+                    const int64_t off = E.take(seg);
+                    if (off < 0) break;
+                    ctx->bqueue.pop_front();
+                    r->state.store(1);
+                    ServeSlot sl;
+                    sl.r = r;
+                    sl.elem0 = off;
+                    sl.seg = seg;
+                    sl.t_admit = now_ms();
+                    E.slots.push_back(sl);
+                    E.dirty = true;
+                }
+            }
+        }
+        for (te_request* r : cancelled) {
+            te_stats S;
+            memset(&S, 0, sizeof(S));
+            if (!ready && init_st != TE_OK && !ctx->stopping)
+                serve_publish(r, init_st, S, "the serving arena could not be allocated");
+            else
+                serve_publish(r, TE_ERR_CANCELLED, S, "request cancelled");
+        }
+        if (ctx->stopping) {
+            while (!E.slots.empty()) serve_finish(E, 0, TE_ERR_CANCELLED, "request cancelled");
+            break;
+        }
+        for (size_t i = 0; i < E.slots.size();) {
+            if (E.slots[i].r->cancel.load()) serve_finish(E, i, TE_ERR_CANCELLED, "request cancelled");
+            else ++i;
+        }
+        if (E.slots.empty()) continue;
+        if (E.dirty) {
+            const te_status cs = serve_compose(E);
+            if (cs != TE_OK) {
+                std::string msg;
+                {
+                    std::lock_guard<std::mutex> lk(ctx->mu);
+                    msg = ctx->err;
+                }
+                while (!E.slots.empty()) {
+                    E.slots[0].idx = -1;
+                    serve_finish(E, 0, cs, msg);
+                }
+                continue;
+            }
+            // requests that failed their start (normalisation, t = 0 done)
+            for (size_t i = 0; i < E.slots.size();) {
+                const DevState& x = E.st_host[E.slots[i].idx];
+                if (x.status != 0) serve_finish(E, i, x.status, device_status_msg(x.status));
+                else if (x.done) serve_finish(E, i, TE_OK, std::string());
+                else ++i;
+            }
+            if (E.dirty) continue;                      // recompose before the round
+        }
+        cudaError_t e = cudaGraphLaunch(E.exec, E.s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E.s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            const std::string msg = std::string("serving round: ") + cudaGetErrorString(e);
+            while (!E.slots.empty()) serve_finish(E, 0, TE_ERR_CUDA, msg);
+            continue;
+        }
+        for (size_t i = 0; i < E.slots.size();) {
+            const DevState& x = E.st_host[E.slots[i].idx];
+            if (x.status != 0) serve_finish(E, i, x.status, device_status_msg(x.status));
+            else if (x.done) serve_finish(E, i, TE_OK, std::string());
+            else ++i;
+        }
+        ctx->qcv.notify_all();
+    }
+    if (ready) {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        ctx->in_use -= (int64_t)E.bytes;
+    }
+    E.release();
 }

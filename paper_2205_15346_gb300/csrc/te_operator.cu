@@ -255,20 +255,20 @@ te_status te_build_operator(te_ctx* ctx, const te_operator_desc* o, te_matrix** 
     auto cleanup = [&]() {
         for (void* q : {(void*)Td, (void*)dtoff, (void*)dmode, (void*)ddag, (void*)cnt, (void*)dcoef,
                         (void*)flags})
-            if (q) cudaFree(q);
+            if (q) dev_free(ctx, q);
     };
     auto fail = [&](te_status st) {
         cleanup();
         te_matrix_free(H);
         return st;
     };
-    cudaError_t e = cudaMalloc(&Td, sizeof(OpTables));
-    if (e == cudaSuccess) e = cudaMalloc(&dtoff, sizeof(int32_t) * (nt + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&dmode, sizeof(int32_t) * std::max(nf, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&ddag, sizeof(int32_t) * std::max(nf, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&dcoef, sizeof(double2) * std::max(nt, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(int32_t) * d);
-    if (e == cudaSuccess) e = cudaMalloc(&flags, sizeof(int) * 4);
+    cudaError_t e = dev_alloc(ctx, &Td, sizeof(OpTables));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &dtoff, sizeof(int32_t) * (nt + 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &dmode, sizeof(int32_t) * std::max(nf, 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &ddag, sizeof(int32_t) * std::max(nf, 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &dcoef, sizeof(double2) * std::max(nt, 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &cnt, sizeof(int32_t) * d);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &flags, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Td, &T, sizeof(OpTables), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dtoff, toff.data(), sizeof(int32_t) * (nt + 1), cudaMemcpyHostToDevice, s);
@@ -294,7 +294,7 @@ te_status te_build_operator(te_ctx* ctx, const te_operator_desc* o, te_matrix** 
     if (e != cudaSuccess) return fail(cuda_error(ctx, e, "operator builder"));
     if (hf[0]) return fail(set_error(ctx, TE_ERR_UNSUPPORTED, "a row has more than 256 contributions"));
     int32_t* rowptr = nullptr;
-    if (cudaMalloc(&rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess) {
+    if (dev_alloc(ctx, &rowptr, sizeof(int32_t) * (d + 1)) != cudaSuccess) {
         cudaGetLastError();
         return fail(set_error(ctx, TE_ERR_OOM, "row pointer"));
     }
@@ -304,8 +304,8 @@ te_status te_build_operator(te_ctx* ctx, const te_operator_desc* o, te_matrix** 
     H->rowptr = rowptr;
     if (st) return fail(st);
     H->nnz = nnz;
-    if (cudaMalloc(&H->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
-        cudaMalloc(&H->val, sizeof(double2) * std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+    if (dev_alloc(ctx, &H->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+        dev_alloc(ctx, &H->val, sizeof(double2) * std::max<int64_t>(nnz, 1)) != cudaSuccess) {
         cudaGetLastError();
         return fail(set_error(ctx, TE_ERR_OOM, "device allocation of the CSR arrays failed"));
     }
@@ -361,9 +361,9 @@ te_status te_operator_occupation(te_ctx* ctx, const te_operator_desc* o, int32_t
     const bool dev = (flags & TE_PTR_DEVICE) != 0;
     OpTables* Td = nullptr;
     double* dst = out;
-    TE_CUDA_TRY(ctx, cudaMalloc(&Td, sizeof(OpTables)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &Td, sizeof(OpTables)));
     cudaError_t e = cudaMemcpyAsync(Td, &T, sizeof(OpTables), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !dev) e = cudaMalloc(&dst, sizeof(double) * (size_t)std::max<int64_t>(d, 1));
+    if (e == cudaSuccess && !dev) e = dev_alloc(ctx, &dst, sizeof(double) * (size_t)std::max<int64_t>(d, 1));
     if (e == cudaSuccess) {
         const int64_t want = (d + TE_BLOCK - 1) / TE_BLOCK;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * 8));
@@ -373,8 +373,8 @@ te_status te_operator_occupation(te_ctx* ctx, const te_operator_desc* o, int32_t
     if (e == cudaSuccess && !dev)
         e = cudaMemcpyAsync(out, dst, sizeof(double) * (size_t)d, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(Td);
-    if (!dev && dst) cudaFree(dst);
+    dev_free(ctx, Td);
+    if (!dev && dst) dev_free(ctx, dst);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_operator_occupation");
     return TE_OK;
 }

@@ -43,7 +43,7 @@ extern "C" te_status te_measure_fp64(te_ctx* ctx, double* tflops) {
     TE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->user_ev, 0));
     const int grid = ctx->num_sms * kBlocksPerSM;
     double* out = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&out, sizeof(double) * (size_t)grid * kThreads));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &out, sizeof(double) * (size_t)grid * kThreads));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -62,7 +62,7 @@ extern "C" te_status te_measure_fp64(te_ctx* ctx, double* tflops) {
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(out);
+    dev_free(ctx, out);
     if (e != cudaSuccess) return cuda_error(ctx, e, "te_measure_fp64");
     const double flop = 2.0 * kChains * (double)kIters * grid * kThreads;
     *tflops = flop / (best * 1e-3) * 1e-12;

@@ -497,11 +497,11 @@ te_status build_dict(te_ctx* ctx, te_matrix* H, VKey** slots_out, uint16_t** slo
     VKey* slots = nullptr;
     uint16_t* slot_idx = nullptr;
     int* flags = nullptr;
-    TE_CUDA_TRY(ctx, cudaMalloc(&slots, sizeof(VKey) * kDictSlots));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &slots, sizeof(VKey) * kDictSlots));
     *slots_out = slots;
-    TE_CUDA_TRY(ctx, cudaMalloc(&slot_idx, sizeof(uint16_t) * kDictSlots));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &slot_idx, sizeof(uint16_t) * kDictSlots));
     *slot_idx_out = slot_idx;
-    TE_CUDA_TRY(ctx, cudaMalloc(&flags, sizeof(int) * 4));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &flags, sizeof(int) * 4));
     *flags_out = flags;
     TE_CUDA_TRY(ctx, cudaMemsetAsync(slots, 0xff, sizeof(VKey) * kDictSlots, s));
     TE_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * 4, s));
@@ -513,8 +513,8 @@ te_status build_dict(te_ctx* ctx, te_matrix* H, VKey** slots_out, uint16_t** slo
     TE_CUDA_TRY(ctx, cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
     TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hf[0] || hf[1] || hf[2] > kDictMax) return TE_OK;
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->dict_a, sizeof(double) * (size_t)(hf[2] + 1)));
-    TE_CUDA_TRY(ctx, cudaMalloc(&H->dict_pq, sizeof(double2) * (size_t)(hf[2] + 1)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &H->dict_a, sizeof(double) * (size_t)(hf[2] + 1)));
+    TE_CUDA_TRY(ctx, dev_alloc(ctx, &H->dict_pq, sizeof(double2) * (size_t)(hf[2] + 1)));
     k_dict_compact<<<1, 1024, 0, s>>>(slots, slot_idx, H->dict_a, H->dict_pq);
     TE_CUDA_TRY(ctx, cudaGetLastError());
     H->dict_n = hf[2];
@@ -537,7 +537,7 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
     int32_t* cnt = nullptr;
     auto cleanup = [&]() {
         for (void* q : {(void*)slots, (void*)slot_idx, (void*)flags, (void*)rowlen, (void*)cnt})
-            if (q) cudaFree(q);
+            if (q) dev_free(ctx, q);
     };
     bool dict = false;
     te_status st = build_dict(ctx, H, &slots, &slot_idx, &flags, &dict);
@@ -546,18 +546,18 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
         return st;
     }
     if (!dict) {
-        if (H->dict_a) cudaFree(H->dict_a);
-        if (H->dict_pq) cudaFree(H->dict_pq);
+        if (H->dict_a) dev_free(ctx, H->dict_a);
+        if (H->dict_pq) dev_free(ctx, H->dict_pq);
         H->dict_a = nullptr;
         H->dict_pq = nullptr;
         H->dict_n = 0;
         H->dict_real = false;
     }
-    cudaError_t e = cudaMalloc(&H->perm, sizeof(int32_t) * (size_t)nslices * 32);
-    if (e == cudaSuccess) e = cudaMalloc(&H->iperm, sizeof(int32_t) * (size_t)d);
-    if (e == cudaSuccess) e = cudaMalloc(&H->sell_off, sizeof(int32_t) * (size_t)(nslices + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&rowlen, sizeof(int32_t) * (size_t)d);
-    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(int32_t) * (size_t)nslices);
+    cudaError_t e = dev_alloc(ctx, &H->perm, sizeof(int32_t) * (size_t)nslices * 32);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &H->iperm, sizeof(int32_t) * (size_t)d);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &H->sell_off, sizeof(int32_t) * (size_t)(nslices + 1));
+    if (e == cudaSuccess) e = dev_alloc(ctx, &rowlen, sizeof(int32_t) * (size_t)d);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &cnt, sizeof(int32_t) * (size_t)nslices);
     // rows past d (in the last slice) map to row 0's length: give perm a valid entry there
     if (e == cudaSuccess) e = cudaMemsetAsync(H->perm, 0, sizeof(int32_t) * (size_t)nslices * 32, s);
     const int64_t want = (d + TE_BLOCK - 1) / TE_BLOCK;
@@ -584,10 +584,10 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
         H->sell_tpt = (int)std::min(4.0, std::max(1.0, floor(t + 0.5)));
     }
     const size_t tot1 = (size_t)std::max<int64_t>(total, 1);
-    e = cudaMalloc(&H->sell_col, sizeof(int32_t) * tot1);
+    e = dev_alloc(ctx, &H->sell_col, sizeof(int32_t) * tot1);
     if (dict) {
-        if (e == cudaSuccess) e = cudaMalloc(&H->sell_idx, sizeof(uint16_t) * tot1);
-        if (e == cudaSuccess) e = cudaMalloc(&H->sell_diag, sizeof(double) * (size_t)d);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &H->sell_idx, sizeof(uint16_t) * tot1);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &H->sell_diag, sizeof(double) * (size_t)d);
         if (e == cudaSuccess) {
             k_sellv_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
                 H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, slots,
@@ -595,8 +595,8 @@ te_status build_sell(te_ctx* ctx, te_matrix* H) {
             e = cudaGetLastError();
         }
     } else {
-        if (e == cudaSuccess) e = cudaMalloc(&H->sell_a, sizeof(double) * tot1);
-        if (e == cudaSuccess) e = cudaMalloc(&H->sell_pq, sizeof(double2) * tot1);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &H->sell_a, sizeof(double) * tot1);
+        if (e == cudaSuccess) e = dev_alloc(ctx, &H->sell_pq, sizeof(double2) * tot1);
         if (e == cudaSuccess) {
             k_sell_fill<<<(int)((nslices * 32 + TE_BLOCK - 1) / TE_BLOCK), TE_BLOCK, 0, s>>>(
                 H->rowptr, H->col, H->val, H->perm, H->iperm, H->sell_off, d, nslices, H->sell_col,

@@ -53,6 +53,8 @@ TE_MODEL_TFIM = 1
 TE_MODEL_XXZDM = 2
 TE_MODEL_BOSE = 3
 TE_MODEL_MEMORY = 4
+TE_SERVE_BATCH = 0
+TE_SERVE_SOLO = 1
 
 
 class te_options(C.Structure):
@@ -98,12 +100,22 @@ class te_operator_desc(C.Structure):
                 ("dagger", C.POINTER(C.c_int32)), ("coef", C.POINTER(C.c_double))]
 
 
+# te_allocator's callbacks (include/te.h)
+TE_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32, C.c_void_p)
+TE_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p)
+
+
+class te_allocator(C.Structure):
+    _fields_ = [("alloc", TE_ALLOC_FN), ("free", TE_FREE_FN), ("user", C.c_void_p)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "te_version": (C.c_char_p, []),
     "te_status_string": (C.c_char_p, [C.c_int32]),
     "te_default_options": (None, [C.POINTER(te_options)]),
     "te_create": (C.c_int32, [C.POINTER(_P), C.c_int32, _P]),
+    "te_create_with_allocator": (C.c_int32, [C.POINTER(_P), C.c_int32, _P, C.POINTER(te_allocator)]),
     "te_destroy": (None, [_P]),
     "te_last_error": (C.c_char_p, [_P]),
     "te_build_csr": (C.c_int32, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_uint32, C.POINTER(_P)]),
@@ -139,6 +151,7 @@ _SIGS = {
     "te_cancel": (C.c_int32, [_P]),
     "te_request_free": (None, [_P]),
     "te_set_memory_budget": (C.c_int32, [_P, C.c_int64]),
+    "te_serve_config": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64]),
 }
 
 _lib = None
@@ -237,9 +250,48 @@ def make_options(**kw) -> te_options:
 
 # ---------------------------------------------------------------- C entry points
 
-def te_create(device: int = 0, stream=None):
+# callbacks handed to te_create_with_allocator, kept alive until te_destroy
+_ALLOCATORS = {}
+
+
+class TorchAllocator:
+    """A te_allocator that takes the library's device memory from PyTorch's
+    caching allocator (torch.cuda.caching_allocator_alloc / _delete), so that the
+    Krylov bases and matrices share the pool torch.cuda.memory_allocated reports.
+    The blocks are allocated on the context's stream, which the library
+    synchronises before it frees them."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.live = {}                        # pointer -> bytes
+
+        def _alloc(user, nbytes, device, stream):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), int(device), int(stream or 0))
+            except Exception:
+                return None
+            self.live[int(ptr)] = int(nbytes)
+            return int(ptr)
+
+        def _free(user, ptr, device, stream):
+            self.live.pop(int(ptr), None)
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._afn = TE_ALLOC_FN(_alloc)
+        self._ffn = TE_FREE_FN(_free)
+        self.struct = te_allocator(self._afn, self._ffn, None)
+
+    def bytes_live(self) -> int:
+        return sum(self.live.values())
+
+
+def te_create(device: int = 0, stream=None, allocator=None):
     """Context on ``device``; ``stream`` is a cudaStream_t handle (int) or None
-    (then torch's current stream on that device, if torch is loaded)."""
+    (then torch's current stream on that device, if torch is loaded).
+    ``allocator``: None (cudaMalloc) or an object with a ``struct`` attribute
+    holding a te_allocator (e.g. TorchAllocator()); it is kept alive until
+    te_destroy."""
     if stream is None:
         try:
             import torch
@@ -248,13 +300,20 @@ def te_create(device: int = 0, stream=None):
         except Exception:
             stream = None
     out = C.c_void_p()
-    s = lib().te_create(C.byref(out), device, C.c_void_p(stream or 0))
+    if allocator is None:
+        s = lib().te_create(C.byref(out), device, C.c_void_p(stream or 0))
+    else:
+        s = lib().te_create_with_allocator(C.byref(out), device, C.c_void_p(stream or 0),
+                                           C.byref(allocator.struct))
     _check(None, s)
+    if allocator is not None:
+        _ALLOCATORS[out.value] = allocator
     return out
 
 
 def te_destroy(ctx) -> None:
     lib().te_destroy(ctx)
+    _ALLOCATORS.pop(ctx.value if isinstance(ctx, C.c_void_p) else ctx, None)
 
 
 def te_last_error(ctx) -> str:
@@ -662,3 +721,9 @@ def te_request_free(req) -> None:
 
 def te_set_memory_budget(ctx, nbytes: int) -> None:
     _check(ctx, lib().te_set_memory_budget(ctx, int(nbytes)))
+
+
+def te_serve_config(ctx, mode: int = 0, m_max: int = 0, capacity: int = 0) -> None:
+    """How te_submit serves requests: TE_SERVE_BATCH (continuous batching) or
+    TE_SERVE_SOLO; m_max / capacity shape the serving arena (0: keep)."""
+    _check(ctx, lib().te_serve_config(ctx, int(mode), int(m_max), int(capacity)))

@@ -97,12 +97,25 @@ def test_binding_structs_match_the_header():
     assert {n for n, _ in structs} >= {"te_options", "te_stats", "te_matrix_info",
                                         "te_model_desc", "te_operator_desc"}
     for name, body in structs:
-        fields = re.findall(r"^\s*(?:const\s+)?([a-z0-9_]+)\s*(\*?)\s*([a-zA-Z0-9_]+);", body, flags=re.M)
+        fields = []
+        for decl in (x.strip() for x in body.split(";") if x.strip()):
+            fp = re.match(r"^.*\(\s*\*\s*([a-zA-Z0-9_]+)\s*\)\s*\((.*)\)$", decl, flags=re.S)
+            if fp:                                   # function pointer: (name, argument count)
+                fields.append(("fn", fp.group(2).count(",") + 1, fp.group(1)))
+                continue
+            f = re.match(r"^(?:const\s+)?([a-z0-9_]+)\s*(\*?)\s*([a-zA-Z0-9_]+)$", decl)
+            assert f, (name, decl)
+            fields.append(f.groups())
         py = getattr(te, name)._fields_
         assert [f[2] for f in fields] == [p[0] for p in py], name
         for (typ, star, fname), (_, pytype) in zip(fields, py):
-            want = C.POINTER(ctype[typ]) if star else ctype[typ]
-            assert pytype == want, (name, fname)
+            if typ == "fn":
+                assert len(pytype._argtypes_) == star, (name, fname)
+            elif typ == "void" and star:
+                assert pytype is C.c_void_p, (name, fname)
+            else:
+                want = C.POINTER(ctype[typ]) if star else ctype[typ]
+                assert pytype == want, (name, fname)
 
 
 def test_binding_signatures_match_the_header():
