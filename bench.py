@@ -177,9 +177,18 @@ _ORACLE_H = {}
 
 
 def oracle_matrix(wl):
+    """The oracle's H (the array-form builders for the bosons and the paper's system,
+    bitwise equal to the row-by-row ones)."""
     from oracle import models
     if wl["name"] not in _ORACLE_H:
-        _ORACLE_H[wl["name"]] = models.build(wl["params"]).to_scipy()
+        p = wl["params"]
+        if p["model"] == "bose":
+            A = models.bose_csr_vec(p)
+        elif p["model"] == "memory":
+            A = models.memory_csr_vec(p)
+        else:
+            A = models.build(p)
+        _ORACLE_H[wl["name"]] = A.to_scipy()
     return _ORACLE_H[wl["name"]]
 
 
@@ -197,26 +206,79 @@ def single_view(wl):
     return v
 
 
-def oracle_sample(wl, max_restarts: int = 1):
+def oracle_sample(wl, max_restarts: int = 1, threads=None):
     """Time the oracle on a bounded sample: its first `max_restarts` restarts of
-    the workload's solve (matrix assembly excluded).  Returns (solves/s estimate,
-    wall seconds, time covered, result)."""
+    the workload's solve (matrix assembly excluded).  threads None: scipy's
+    product on one thread (the oracle as it stands, the paper's setting); a
+    count: the oracle's C product on that many threads.  Returns (solves/s
+    estimate, wall seconds, time covered, result)."""
     from oracle import krylov
     A = oracle_matrix(wl)
     v0 = W.initial_vector(wl["v0"], wl["d"])
     t0 = time.perf_counter()
-    res = krylov.evolve(A, v0, wl["t"], wl["tol"], wl["m"], max_restarts=max_restarts)
+    res = krylov.evolve(A, v0, wl["t"], wl["tol"], wl["m"], max_restarts=max_restarts, threads=threads)
     wall = time.perf_counter() - t0
     covered = abs(res.t_reached)
     return (covered / wl["t"]) / wall, wall, covered, res
 
 
-def cpu_baseline_entry(wl):
-    rate, wall, covered, res = oracle_sample(wl, 1)
-    return {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (numpy/scipy, 1 thread) first restart of the {wl['name']} solve: "
-                       f"{res.matvecs} matvecs, t advanced {covered:.4g} of {wl['t']} in {wall:.1f} s; "
-                       f"solves/s = (fraction of t covered) / wall time")}
+def sm_mhz_now(gpu: int) -> float:
+    """Current SM clock (MHz) from nvidia-smi; the maximum, 2070, if unavailable."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu), "--query-gpu=clocks.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=10).stdout
+        return float(out.strip().splitlines()[0])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return 2070.0
+
+
+def host_cpu():
+    """Core count and CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": os.uname().machine}
+
+
+def cpu_baseline_entry(wl, restarts: int = 5):
+    """The oracle's first `restarts` restarts on one thread and on all host cores;
+    solves/s = (fraction of t covered) / wall time (a per-restart rate)."""
+    from oracle import native
+    info = host_cpu()
+    n = info["nproc"] or 1
+    r1, w1, c1, res1 = oracle_sample(wl, restarts)
+    entry = {"unit": "solves/s", "kind": "oracle", "cpu_model": info["cpu_model"],
+             "nproc": n, "machine": info["machine"],
+             "one_thread": {"value": r1, "cores": 1, "wall_s": w1, "restarts": res1.restarts,
+                            "t_covered": c1}}
+    if native.available():
+        rn, wn, cn, resn = oracle_sample(wl, restarts, threads=n)
+        entry.update({"value": rn, "cores": n, "threads": n,
+                      "all_cores": {"value": rn, "cores": n, "wall_s": wn, "restarts": resn.restarts,
+                                    "t_covered": cn}})
+    else:
+        entry.update({"value": r1, "cores": 1, "threads": 1})
+    entry["sample"] = (f"per-restart rate: the oracle's first {res1.restarts} restarts of the "
+                       f"{wl['name']} solve ({res1.matvecs} matvecs, t advanced {c1:.4g} of {wl['t']}), "
+                       f"on 1 thread (numpy/scipy, {w1:.1f} s) and on all {n} cores (the oracle's "
+                       f"C product on {n} threads, vector work numpy on one); "
+                       f"solves/s = (fraction of t covered) / wall time")
+    return entry
 
 
 def oracle_multi_sample(wl):
@@ -243,22 +305,28 @@ def run_reference(args):
     if "problems" in W.workload(args.workload):
         return run_reference_multi(args)
     wl = single_view(W.workload(args.workload))
+    from oracle import native
+    info = host_cpu()
+    threads = info["nproc"] if native.available() else None
     rates, walls = [], []
     for i in range(args.warmup + args.steps):
-        rate, wall, covered, res = oracle_sample(wl, 1)
+        rate, wall, covered, res = oracle_sample(wl, 1, threads=threads)
         if i >= args.warmup:
             rates.append(rate)
             walls.append(wall)
     value = float(np.mean(rates))
+    cores = threads or 1
     line = {
         "metric": METRIC, "impl": "reference", "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * float(np.mean(walls)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
         "config": config_block(wl, args),
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step: the oracle's first restart of the workload solve "
-                                   "(1 thread); solves/s = fraction of t covered / wall time"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": info["cpu_model"], "nproc": info["nproc"],
+                         "sample": (f"each step: the oracle's first restart of the workload solve "
+                                    f"(its C product on {cores} threads); solves/s = fraction of t "
+                                    f"covered / wall time")},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -906,21 +974,42 @@ def run_scaling(args):
             v0 = W.initial_vector(q["v0"], d, index_of=lambda o: te.te_model_basis_index(p, o))
             vin = torch.from_numpy(v0).cuda()
             vout = torch.empty_like(vin)
-            for _ in range(args.warmup):
-                te.te_evolve(ctx, H, vin, t, tol, m, v_out=vout)
-            torch.cuda.synchronize()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record()
-            for _ in range(args.steps):
-                _, st, _ = te.te_evolve(ctx, H, vin, t, tol, m, v_out=vout)
-            ev1.record()
-            torch.cuda.synchronize()
-            sec = ev0.elapsed_time(ev1) / 1000.0 / args.steps
+
+            def timed(opt):
+                for _ in range(args.warmup):
+                    te.te_evolve(ctx, H, vin, t, tol, m, opt, v_out=vout)
+                torch.cuda.synchronize()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                for _ in range(args.steps):
+                    _, st, _ = te.te_evolve(ctx, H, vin, t, tol, m, opt, v_out=vout)
+                ev1.record()
+                torch.cuda.synchronize()
+                return ev0.elapsed_time(ev1) / 1000.0 / args.steps, st
+
+            sec, st = timed(te.make_options())
             fit = PAPER_FIT_A * d ** PAPER_FIT_B
-            rows.append({"K": p["K"], "N0": p["N0"], "d": d, "nnz": te.te_matrix_info_get(H)["nnz"],
-                         "gpu_s_per_solve": sec, "paper_fit_cpu_s": fit, "ratio_to_fit": fit / sec,
-                         "restarts": st["restarts"], "err_bound": st["err_bound"]})
+            row = {"K": p["K"], "N0": p["N0"], "d": d, "nnz": te.te_matrix_info_get(H)["nnz"],
+                   "gpu_s_per_solve": sec, "paper_fit_cpu_s": fit, "ratio_to_fit": fit / sec,
+                   "restarts": st["restarts"], "err_bound": st["err_bound"]}
+            if args.quad_study:
+                # Sec. 4: Gauss-Legendre against tanh-sinh for the error integral.  The step
+                # kernel's SM cycles over the solve give its share of the solve time.
+                quad = {}
+                outs = {}
+                for name in ("tanh-sinh", "gauss"):
+                    qs, qst = timed(te.make_options(quad=name))
+                    k3_ms = (qst["eig_mcycles"] + qst["search_mcycles"]) * 1e3 / sm_mhz_now(local)
+                    quad[name] = {"s_per_solve": qs, "solves_per_s": 1.0 / qs,
+                                  "restarts": qst["restarts"], "quad_integrals": qst["quad_integrals"],
+                                  "quad_nodes": qst["quad_nodes"], "step_kernel_ms": k3_ms,
+                                  "step_kernel_share": k3_ms / (1e3 * qs), "err_bound": qst["err_bound"]}
+                    outs[name] = vout.clone()
+                quad["norm_diff"] = torch.linalg.vector_norm(outs["gauss"] - outs["tanh-sinh"]).item()
+                quad["norm_diff_over_tol"] = quad["norm_diff"] / tol
+                row["quadrature"] = quad
+            rows.append(row)
             te.te_matrix_free(H)
     te.te_destroy(ctx)
     # the GPU's own power law over the four fitted sizes
@@ -946,85 +1035,135 @@ def run_scaling(args):
 
 
 def run_serve(args):
-    """Serving: a Poisson stream of mixed requests through te_submit / te_poll,
-    against the same requests solved one at a time (te_evolve)."""
+    """Serving (the request-stream configuration): Poisson arrivals of mixed
+    requests through te_submit (continuous batching), against the one-at-a-time
+    GPU method (te_evolve, one request after the other, first come first served)
+    on the same arrivals.
+
+    The one-at-a-time service time s_i of every request is measured by solving
+    the requests one after another; its latencies at an arrival process a_i are
+    then those of a single FIFO server: f_i = max(a_i, f_{i-1}) + s_i,
+    latency_i = f_i - a_i (exact for a server that runs one solve at a time).
+    Capacity = 1 / mean(s_i); each load sets the arrival rate to load x capacity.
+    Both sides take host vectors and return host vectors."""
     import torch
     from paper_2205_15346_gb300 import te
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     ctx = te.te_create(local)
+    te.te_serve_config(ctx, te.TE_SERVE_BATCH, 40, args.arena, args.large_nnz)
+    m = 40
     pool = []
     for fam, p in W.serve_pool():
         H = te.te_build_model(ctx, p)
         te.te_matrix_tune(ctx, H)
-        pool.append((H, te.te_matrix_info_get(H)["d"], p))
-    reqs = W.serve_requests(args.requests)
-    m = 40
-
-    def v0_for(k, seed):
-        H, d, p = pool[k]
-        return W.random_state(seed, d)
-
-    vins = [v0_for(k, sd) for (k, t, tol, sd, gap) in reqs]
-    # warm-up: one solve per pool entry (plans, graphs)
-    for H, d, p in pool:
-        te.te_evolve(ctx, H, W.random_state(1, d), 1.0, 1e-8, m)
-    # one at a time
-    solo_ms, solo_out = [], []
-    t0 = time.perf_counter()
-    for (k, t, tol, sd, gap), v in zip(reqs, vins):
+        d = te.te_matrix_info_get(H)["d"]
+        # four seeded initial states per Hamiltonian; request i takes variant i mod 4
+        pool.append((H, d, [W.random_state(600 + 4 * len(pool) + j, d) for j in range(4)]))
+    loads = [float(x) for x in args.loads.split(",")]
+    counts = ([int(x) for x in args.requests_per_load.split(",")] if args.requests_per_load
+              else [args.requests] * len(loads))
+    if len(counts) != len(loads):
+        raise SystemExit("--requests-per-load needs one count per load")
+    n_max = max(counts)
+    reqs = W.serve_requests(n_max)
+    vin = lambda i: pool[reqs[i][0]][2][i % 4]
+    outbuf = {d: np.empty(d, dtype=np.complex128) for _, d, _ in pool}
+    check = set(range(0, n_max, max(1, n_max // 48)))      # results compared alone vs mixed
+    clk = ClockSampler(local).__enter__()          # sampled over warm-up, solo and served runs
+    # warm-up: a solve per Hamiltonian (plans, graphs) and a few served requests (arena, graphs)
+    for H, d, vs in pool:
+        te.te_evolve(ctx, H, vs[0], 1.0, 1e-8, m)
+    warm = [te.te_submit(ctx, pool[k][0], pool[k][2][0], 1.0, 1e-8, m) for k in range(0, len(pool), 5)]
+    for r in warm:
+        te.te_wait(r, -1.0, None)
+        te.te_request_free(r)
+    # one at a time: service time of every request
+    solo_s, solo_out = [], {}
+    t_solo = time.perf_counter()
+    for i, (k, t, tol, sd, gap) in enumerate(reqs):
         a = time.perf_counter()
-        out, st, _ = te.te_evolve(ctx, pool[k][0], v, t, tol, m)
-        solo_ms.append(1000.0 * (time.perf_counter() - a))
-        solo_out.append(out)
-    solo_total = time.perf_counter() - t0
-    mean_solve = solo_total / len(reqs)
-    # served: submit at Poisson arrival times (all at t = 0 when --load 0), poll
-    if args.load > 0:
-        rate = args.load / mean_solve              # arrivals per second
-        arrivals = np.cumsum([gap / rate for (k, t, tol, sd, gap) in reqs])
-    else:
-        rate = float("inf")
-        arrivals = np.zeros(len(reqs))
-    pending, lat, done_out = {}, [0.0] * len(reqs), [None] * len(reqs)
-    nxt = 0
-    t0 = time.perf_counter()
-    while nxt < len(reqs) or pending:
-        now = time.perf_counter() - t0
-        while nxt < len(reqs) and arrivals[nxt] <= now:
-            k, t, tol, sd, gap = reqs[nxt]
-            pending[nxt] = te.te_submit(ctx, pool[k][0], vins[nxt], t, tol, m)
-            nxt += 1
-        for i in list(pending):
-            s, st = te.te_poll(pending[i], None)
-            if s != te.TE_PENDING:
-                out = np.empty(pool[reqs[i][0]][1], dtype=np.complex128)
+        out, st, _ = te.te_evolve(ctx, pool[k][0], vin(i), t, tol, m, v_out=outbuf[pool[k][1]])
+        solo_s.append(time.perf_counter() - a)
+        if i in check:
+            solo_out[i] = out.copy()
+    solo_wall = time.perf_counter() - t_solo
+    solo_s = np.array(solo_s)
+    cap_per_s = 1.0 / float(np.mean(solo_s))
+    runs, worst = [], 0.0
+    for load, n in zip(loads, counts):
+        rate = load * cap_per_s
+        arrivals = np.cumsum([reqs[i][4] / rate for i in range(n)])
+        arrivals -= arrivals[0]
+        # the one-at-a-time server on these arrivals
+        f, lat_solo = 0.0, []
+        for i in range(n):
+            f = max(arrivals[i], f) + solo_s[i]
+            lat_solo.append(f - arrivals[i])
+        solo_span = f - arrivals[0]
+        # served: submit at the arrival times, poll, copy each result out
+        pending, lat = {}, np.zeros(n)
+        nxt = 0
+        t0 = time.perf_counter()
+        while nxt < n or pending:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[nxt] <= now:
+                k, t, tol, sd, gap = reqs[nxt]
+                pending[nxt] = te.te_submit(ctx, pool[k][0], vin(nxt), t, tol, m)
+                nxt += 1
+            for i in list(pending):
+                if te.te_poll(pending[i], None)[0] == te.TE_PENDING:
+                    continue
+                k = reqs[i][0]
+                out = outbuf[pool[k][1]]
                 s, st = te.te_poll(pending[i], out)
                 if s != te.TE_OK:
-                    raise RuntimeError(f"request {i} failed: {te.te_status_string(s)}")
-                lat[i] = 1000.0 * (time.perf_counter() - t0 - arrivals[i])
-                done_out[i] = out
+                    raise RuntimeError(f"request {i} failed: {te.te_status_string(s)} "
+                                       f"({te.te_last_error(ctx)})")
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+                if i in solo_out:
+                    worst = max(worst, float(np.linalg.norm(out - solo_out[i])) / reqs[i][2])
                 te.te_request_free(pending.pop(i))
-        time.sleep(0.0002)
-    served_total = time.perf_counter() - t0
-    worst = max(float(np.linalg.norm(a - b)) / r[2] for a, b, r in zip(done_out, solo_out, reqs))
+            time.sleep(0.0002)
+        span = time.perf_counter() - t0
+        runs.append({
+            "load": load, "requests": n, "arrival_rate_per_s": rate,
+            "served": {"solves_per_s": n / span, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                       "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)),
+                       "latency_ms_mean": 1e3 * float(np.mean(lat))},
+            "one_at_a_time": {"solves_per_s": n / solo_span,
+                              "latency_ms_p50": 1e3 * float(np.percentile(lat_solo, 50)),
+                              "latency_ms_p99": 1e3 * float(np.percentile(lat_solo, 99)),
+                              "latency_ms_mean": 1e3 * float(np.mean(lat_solo))},
+        })
+    clk.__exit__(None, None, None)
+    head = runs[loads.index(0.8)] if 0.8 in loads else runs[0]
+    lane = (f"large lane (one at a time, solo solve) for nnz >= {args.large_nnz}" if args.large_nnz > 0
+            else "every request batched")
     line = {
-        "metric": METRIC, "mode": "serve", "value": len(reqs) / served_total, "unit": "solves/s",
-        "n_gpus": 1, "steps": len(reqs), "warmup": len(pool), "higher_is_better": True,
-        "ms_per_step": 1000.0 * served_total / len(reqs), "dtype": "complex128",
-        "data": "synthetic Poisson request mix (workloads.serve_requests, seed 5)",
-        "config": {"workload": (f"serving: {len(reqs)} requests over 12 Hamiltonians (TFIM/XXZ-DM "
-                                "2^10..2^22, bosons 1.2e4..1.1e6), t log-U[1,100], tol in "
-                                "{1e-6,1e-8,1e-10}, m=40"),
-                   "arrival_rate_per_s": rate if rate != float("inf") else None,
-                   "load_vs_one_at_a_time": args.load if args.load > 0 else "all at once"},
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "one_at_a_time": {"solves_per_s": len(reqs) / solo_total,
-                          "latency_ms_p50": float(np.percentile(solo_ms, 50)),
-                          "latency_ms_p99": float(np.percentile(solo_ms, 99))},
+        "metric": METRIC, "mode": "serve", "value": head["served"]["solves_per_s"], "unit": "solves/s",
+        "n_gpus": 1, "steps": head["requests"], "warmup": len(pool) + len(warm),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": 1e3 / head["served"]["solves_per_s"], "dtype": "complex128",
+        "data": ("synthetic Poisson request mix (workloads.serve_requests, seed 5; four seeded "
+                 "initial states per Hamiltonian)"),
+        "config": {"workload": ("serving: Poisson requests over 2 x 16 Hamiltonians (spin: TFIM/XXZ-DM "
+                                "L 10..22; bosons: K=12 N=6 and K=14 N=6..10), half of each, "
+                                "t log-U[1,100], tol in {1e-6,1e-8,1e-10}, m=40; continuous batching "
+                                f"(arena {args.arena} elements per Krylov column); " + lane),
+                   "loads": loads, "requests_per_load": counts,
+                   "l2": "inputs larger than L2 for the large requests; no flush"},
+        "latency_ms": {"p50": head["served"]["latency_ms_p50"], "p99": head["served"]["latency_ms_p99"]},
+        "one_at_a_time": {"capacity_solves_per_s": cap_per_s, "requests_timed": n_max,
+                          "wall_s": solo_wall,
+                          "service_ms_p50": 1e3 * float(np.percentile(solo_s, 50)),
+                          "service_ms_p99": 1e3 * float(np.percentile(solo_s, 99))},
+        "runs": runs,
         "max_diff_over_tol_vs_alone": worst,
+        "compared_alone_vs_mixed": len(check),
+        "clocks": clk.summary(),
     }
-    for H, d, p in pool:
+    for H, d, vs in pool:
         te.te_matrix_free(H)
     te.te_destroy(ctx)
     print(json.dumps(line), flush=True)
@@ -1039,10 +1178,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIBE) + ["serve_mix"])
-    ap.add_argument("--requests", type=int, default=32, help="serve_mix: number of requests")
-    ap.add_argument("--load", type=float, default=0.8,
-                    help="serve_mix: arrival rate as a fraction of one-at-a-time capacity "
-                         "(0: every request arrives at once)")
+    ap.add_argument("--requests", type=int, default=200, help="serve_mix: requests per load")
+    ap.add_argument("--requests-per-load", default="",
+                    help="serve_mix: comma-separated request counts, one per load")
+    ap.add_argument("--loads", default="0.5,0.8,1.0,1.2",
+                    help="serve_mix: arrival rates as fractions of one-at-a-time capacity")
+    ap.add_argument("--quad-study", action="store_true",
+                    help="memory_scaling: also time every size with Gauss-Legendre and tanh-sinh")
+    ap.add_argument("--large-nnz", type=int, default=1 << 24,
+                    help="serve_mix: large-lane threshold on nnz (negative: batch everything)")
+    ap.add_argument("--arena", type=int, default=1 << 25,
+                    help="serve_mix: elements per Krylov column of the serving arena")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)     # at least three untimed warm-up steps
     if args.impl == "reference":

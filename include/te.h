@@ -504,9 +504,14 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
  *     ((d rounded up to 32) elements of the arena) is free, and a finished
  *     request leaves at the end of its round.  The result equals te_evolve's
  *     within the same error bound (the same steps, reductions summed in another
- *     order).  Requests with reorthogonalisation, the CSR kernel (spmv_lanes),
- *     TE_OPT_PROFILE, m above the arena depth or d above its capacity go to
- *     the solo workers instead.
+ *     order).  Requests whose H holds at least the large-lane threshold of
+ *     stored entries (default 2^24; one restart of such a request fills the
+ *     GPU by itself) run in the large lane instead: one at a time, first come
+ *     first served, as a solo solve on its own stream beside the batch (that
+ *     stream has the highest priority, the batch's the lowest), so that large
+ *     requests neither slow each other down nor wait behind small ones.  Requests with reorthogonalisation, the CSR kernel (spmv_lanes),
+ *     TE_OPT_PROFILE, m above the arena depth or d above its capacity take
+ *     the large lane too.
  *   TE_SERVE_SOLO: up to 8 worker threads each admit the oldest queued request
  *     once its device footprint ((m+1) d 16 bytes plus reduction scratch)
  *     fits the context's memory budget, and run it on their own stream, one
@@ -531,14 +536,17 @@ te_status te_set_memory_budget(te_ctx* ctx, int64_t bytes);
 #define TE_SERVE_BATCH 0           /* continuous batching of requests (default) */
 #define TE_SERVE_SOLO  1           /* one solve per worker thread and stream */
 /* How te_submit serves requests.  m_max is the Krylov depth of the serving
- * arena (1..TE_M_MAX; 0: keep, default 40) and capacity the number of vector
+ * arena (1..TE_M_MAX; 0: keep, default 40), capacity the number of vector
  * elements per Krylov column it holds (0: keep; default
- * min(2^24, budget / (16 (m_max + 1) + 8)) at first use).  The arena takes
+ * min(2^24, budget / (16 (m_max + 1) + 8)) at first use), and large_nnz the
+ * large-lane threshold on the stored entries of H (0: keep, default 2^24;
+ * negative: no large lane, every eligible request is batched).  The arena takes
  * (m_max + 1) capacity 16 + capacity 8 bytes once the first batched request
  * arrives, counts against the memory budget, and is released by te_destroy.
  * Allowed only while no request is queued or running (else
  * TE_ERR_INVALID_ARG). */
-te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity);
+te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity,
+                          int64_t large_nnz);
 
 #ifdef __cplusplus
 }

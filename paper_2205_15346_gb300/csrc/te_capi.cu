@@ -1126,7 +1126,8 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
 
 // ------------------------------------------------------------------ requests
 
-te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity) {
+te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity,
+                          int64_t large_nnz) {
     if (!ctx || (mode != TE_SERVE_BATCH && mode != TE_SERVE_SOLO) || m_max < 0 || m_max > TE_M_MAX ||
         capacity < 0)
         return TE_ERR_INVALID_ARG;
@@ -1137,6 +1138,7 @@ te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capa
         return set_error(ctx, TE_ERR_INVALID_ARG,
                          "te_serve_config: the serving arena exists; set its shape before the first request");
     ctx->serve_mode = mode;
+    if (large_nnz) ctx->serve_large_nnz = large_nnz;
     if (m_max) ctx->serve_m = m_max;
     if (capacity) ctx->serve_cap = std::max<int64_t>(32, capacity / 32 * 32);
     return TE_OK;
@@ -1268,7 +1270,11 @@ namespace {
 void worker_loop(te_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStream_t s = nullptr;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    // the highest stream priority: a large-lane solve keeps the SMs it needs while the
+    // batch (lowest priority) takes what is left
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
     for (;;) {
         te_request* r = nullptr;
         bool counted = false;                 // r's footprint is in ctx->in_use
@@ -1278,7 +1284,8 @@ void worker_loop(te_ctx* ctx) {
                 if (ctx->stopping) return true;
                 if (ctx->queue.empty()) return false;
                 te_request* f = ctx->queue.front();
-                return ctx->in_use == 0 || ctx->in_use + (int64_t)f->footprint <= ctx->budget;
+                if (ctx->serve_mode == TE_SERVE_BATCH && ctx->solo_running > 0) return false;
+                return ctx->solo_running == 0 || ctx->in_use + (int64_t)f->footprint <= ctx->budget;
             });
             if (ctx->stopping && ctx->queue.empty()) break;
             if (ctx->stopping) {
@@ -1289,6 +1296,7 @@ void worker_loop(te_ctx* ctx) {
                 r = ctx->queue.front();
                 ctx->queue.pop_front();
                 ctx->in_use += (int64_t)r->footprint;
+                ctx->solo_running += 1;
                 counted = true;
             }
             r->state.store(1);
@@ -1318,7 +1326,10 @@ void worker_loop(te_ctx* ctx) {
         }
         {
             std::lock_guard<std::mutex> lk(ctx->qmu);
-            if (counted) ctx->in_use -= (int64_t)r->footprint;
+            if (counted) {
+                ctx->in_use -= (int64_t)r->footprint;
+                ctx->solo_running -= 1;
+            }
             ctx->pending -= 1;
         }
         ctx->qcv.notify_all();

@@ -207,6 +207,8 @@ struct te_ctx {
     int serve_m = 40;                // Krylov depth of the serving arena
     int64_t serve_cap = 0;           // elements per arena column (0: from the budget at first use)
     int64_t pending = 0;             // requests submitted and not yet finished
+    int64_t serve_large_nnz = 1ll << 24;   // batch mode: H with this many entries takes the large lane
+    int solo_running = 0;            // requests the solo workers are running
     bool stopping = false;
     int64_t budget = 0;
     int64_t in_use = 0;

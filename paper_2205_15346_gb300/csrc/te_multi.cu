@@ -799,7 +799,9 @@ struct ServeEngine {
         depth = m_max;
         cap = capacity / 32 * 32;
         npart = (size_t)(cap / 32 + 2 * TE_MULTI_MAX + 1);
-        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        int lo = 0, hi = 0;                         // the batch runs at the lowest priority
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, lo);
         if (e == cudaSuccess) e = dev_alloc(ctx, &V, sizeof(double2) * (size_t)(depth + 1) * (size_t)cap);
         if (e == cudaSuccess) e = dev_alloc(ctx, &S, sizeof(double) * (size_t)cap);
         if (e == cudaSuccess) e = dev_alloc(ctx, &partials, sizeof(double) * npart);
@@ -1014,7 +1016,8 @@ const char* device_status_msg(te_status s) {
 bool serve_eligible(const te_ctx* ctx, const te_request* r) {
     return ctx->serve_mode == TE_SERVE_BATCH && r->opt.reorth == TE_REORTH_NONE &&
            r->opt.spmv_lanes == 0 && !(r->opt.flags & TE_OPT_PROFILE) && r->m <= ctx->serve_m &&
-           r->H->sell_off != nullptr && (r->H->d + 31) / 32 * 32 <= ctx->serve_cap;
+           r->H->sell_off != nullptr && (r->H->d + 31) / 32 * 32 <= ctx->serve_cap &&
+           (ctx->serve_large_nnz <= 0 || r->H->nnz < ctx->serve_large_nnz);
 }
 
 // The serving loop (one thread per context, started by the first batched request).

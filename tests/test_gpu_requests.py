@@ -233,3 +233,48 @@ def test_cancel_running_batched_request(te):
             te.te_matrix_free(H)
     finally:
         te.te_destroy(ctx)
+
+
+def test_large_lane_runs_large_requests_one_at_a_time(te):
+    """With the large-lane threshold at 2^17 stored entries, TFIM L = 14 requests
+    (245,760 entries) run one at a time as solo solves beside the batch (bitwise
+    te_evolve's result, finished in arrival order), while small requests are
+    batched and finish within the error bound of their solo solves."""
+    import time
+    ctx = te.te_create(0)
+    try:
+        te.te_serve_config(ctx, te.TE_SERVE_BATCH, 40, 1 << 20, 1 << 17)
+        Hl = te.te_build_model(ctx, W.tfim_params(14, 170))
+        Hs = te.te_build_model(ctx, W.xxzdm_params(10, 171))
+        try:
+            vl = [W.random_state(172 + i, 1 << 14) for i in range(3)]
+            vs = [W.random_state(180 + i, 1 << 10) for i in range(6)]
+            solo_l = [te.te_evolve(ctx, Hl, v, 8.0, 1e-8, 40)[0] for v in vl]
+            solo_s = [te.te_evolve(ctx, Hs, v, 5.0, 1e-8, 40)[0] for v in vs]
+            rl = [te.te_submit(ctx, Hl, v, 8.0, 1e-8, 40) for v in vl]
+            rs = [te.te_submit(ctx, Hs, v, 5.0, 1e-8, 40) for v in vs]
+            finish = []
+            pending = set(range(len(rl)))
+            t0 = time.perf_counter()
+            while pending and time.perf_counter() - t0 < 120.0:
+                for i in sorted(pending):
+                    if te.te_poll(rl[i], None)[0] != te.TE_PENDING:
+                        finish.append(i)
+                        pending.discard(i)
+                time.sleep(0.0005)
+            assert finish == [0, 1, 2]                 # first come, first served
+            for r, ref in zip(rl, solo_l):
+                out = np.empty(1 << 14, dtype=np.complex128)
+                s, _ = te.te_wait(r, 120000.0, out)
+                assert s == te.TE_OK and np.array_equal(out, ref)
+            for r, ref in zip(rs, solo_s):
+                out = np.empty(1 << 10, dtype=np.complex128)
+                s, _ = te.te_wait(r, 120000.0, out)
+                assert s == te.TE_OK and np.linalg.norm(out - ref) <= 2e-8 + 1e-12
+            for r in rl + rs:
+                te.te_request_free(r)
+        finally:
+            te.te_matrix_free(Hl)
+            te.te_matrix_free(Hs)
+    finally:
+        te.te_destroy(ctx)

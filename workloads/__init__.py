@@ -210,15 +210,26 @@ def initial_vector(spec, d: int, index_of=None) -> np.ndarray:
 
 # ---------------------------------------------------------------- serving mix
 
+SERVE_POOL_SIZE = 16          # Hamiltonians per family in the serving mix
+SERVE_BOSE_SHAPES = ((12, 6), (14, 6), (14, 7), (14, 8), (14, 9), (14, 10))
+
+
 def serve_pool() -> list:
-    """Hamiltonians a serving stream draws from: spin chains of 2^10..2^22
-    states and number-conserving bosons of 1.2e4..1.1e6 states."""
+    """The Hamiltonians a serving stream draws from: two families of 16.
+
+    spin: TFIM (even slots) and XXZ-DM (odd slots) chains with L spread evenly
+    over 10..22 (2^10..2^22 states); bose: number-conserving bosons cycling over
+    (K, N) = (12, 6), (14, 6), (14, 7), (14, 8), (14, 9), (14, 10), i.e.
+    12,376..1,144,066 states.  Entries are (family, parameters)."""
     pool = []
-    for i, L in enumerate((10, 14, 18, 22)):
-        pool.append(("tfim", tfim_params(L, seed=500 + i)))
-    for i, L in enumerate((12, 16, 20, 22)):
-        pool.append(("xxzdm", xxzdm_params(L, seed=510 + i)))
-    for i, (K, N) in enumerate(((12, 6), (14, 6), (14, 8), (14, 10))):
+    for i in range(SERVE_POOL_SIZE):
+        L = 10 + int(round(12 * i / (SERVE_POOL_SIZE - 1)))
+        if i % 2 == 0:
+            pool.append(("spin", tfim_params(L, seed=500 + i)))
+        else:
+            pool.append(("spin", xxzdm_params(L, seed=500 + i)))
+    for i in range(SERVE_POOL_SIZE):
+        K, N = SERVE_BOSE_SHAPES[i % len(SERVE_BOSE_SHAPES)]
         pool.append(("bose", bose_params(K, N, seed=520 + i)))
     return pool
 
@@ -226,17 +237,19 @@ def serve_pool() -> list:
 def serve_requests(n: int, seed: int = 5) -> list:
     """n requests: (pool index, t, tol, v0 seed, unit-rate exponential gap).
 
-    t ~ log-uniform on [1, 100], tol uniform over {1e-6, 1e-8, 1e-10}; the gap is
-    an Exp(1) draw that the caller divides by the arrival rate.
-    """
-    u = uniform(seed, 4 * n)
-    npool = len(serve_pool())
+    Half spin, half bosons (one uniform draw picks the family, the next the
+    Hamiltonian within it), t ~ log-uniform on [1, 100], tol uniform over
+    {1e-6, 1e-8, 1e-10}; the gap is an Exp(1) draw that the caller divides by
+    the arrival rate.  The draws are counter-based, so the first k requests of
+    any n are the same."""
+    u = uniform(seed, 5 * n)
     out = []
     for i in range(n):
-        k = min(int(u[4 * i] * npool), npool - 1)
-        t = float(10.0 ** (2.0 * u[4 * i + 1]))
-        tol = (1e-6, 1e-8, 1e-10)[min(int(u[4 * i + 2] * 3), 2)]
-        gap = float(-np.log1p(-u[4 * i + 3]))
+        fam = 0 if u[5 * i] < 0.5 else 1
+        k = fam * SERVE_POOL_SIZE + min(int(u[5 * i + 1] * SERVE_POOL_SIZE), SERVE_POOL_SIZE - 1)
+        t = float(10.0 ** (2.0 * u[5 * i + 2]))
+        tol = (1e-6, 1e-8, 1e-10)[min(int(u[5 * i + 3] * 3), 2)]
+        gap = float(-np.log1p(-u[5 * i + 4]))
         out.append((k, t, tol, 700 + i, gap))
     return out
 
