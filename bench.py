@@ -40,7 +40,8 @@ WORKLOAD = "xxzdm_L22"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_spmv_sellv_xxzdm_L22.md")
 # committed ncu summaries of the dominant kernel (K1) per single-solve workload
 K1_SUMMARIES = {"xxzdm_L22": PROFILE_SUMMARY,
-                "memory_K10": os.path.join(ROOT, "profiles", "k_spmv_sellr_memory_K10.md")}
+                "memory_K10": os.path.join(ROOT, "profiles", "k_spmv_sellr_memory_K10.md"),
+                "random_L20": os.path.join(ROOT, "profiles", "k_spmv_sell_random_L20.md")}
 K1_SOURCES = [os.path.join(ROOT, "paper_2205_15346_gb300", "csrc", f)
               for f in ("te_sell.cu", "te_slices.cuh")]
 # FP64 issue rate of GB300: 2 DFMA lanes per SM per cycle (ncu reports a sustained
@@ -182,7 +183,9 @@ def oracle_matrix(wl):
     from oracle import models
     if wl["name"] not in _ORACLE_H:
         p = wl["params"]
-        if p["model"] == "bose":
+        if p["model"] == "coo":
+            A = models.coo_to_csr(wl["d"], *W.random_hermitian_coo(p["L"], p["seed"]))
+        elif p["model"] == "bose":
             A = models.bose_csr_vec(p)
         elif p["model"] == "memory":
             A = models.memory_csr_vec(p)
@@ -359,6 +362,8 @@ def run_reference_multi(args):
 
 
 DESCRIBE = {
+    "random_L20": ("general complex Hermitian matrix from COO (random value per coupled pair, "
+                   "spin-chain pattern) d=1048576, nnz=11534336, full-value sliced copy, random v0"),
     "xxzdm_L22": "XXZ-DM chain L=22 periodic, d=4194304, nnz=50331648, Neel v0",
     "xxzdm_L20": "XXZ-DM chain L=20 periodic, d=1048576, nnz=11534336, random v0",
     "tfim_L12": "TFIM chain L=12 open, d=4096, nnz=53248, random v0",
@@ -398,6 +403,49 @@ def config_block(wl, args):
 
 # ---------------------------------------------------------------- GPU arm
 
+# The other configurations, each run in a child process of its own after the headline
+# workload (a failure there is recorded, not raised): configs 1, 3a, 3b and 4 with a few
+# timed steps, the general complex CSR, and a short request stream at 0.8 x capacity.
+OTHER_CONFIGS = [
+    ("tfim_L12", ["--steps", "20", "--warmup", "3"]),
+    ("bose_K14_N10", ["--steps", "3", "--warmup", "3"]),
+    ("batch_xxzdm_L20_x64", ["--steps", "3", "--warmup", "3"]),
+    ("tfim_multi_x32", ["--steps", "5", "--warmup", "3"]),
+    ("random_L20", ["--steps", "5", "--warmup", "3"]),
+    ("serve_mix", ["--requests", "80", "--loads", "0.8"]),
+]
+
+
+def other_configs():
+    out = {}
+    for name, extra in OTHER_CONFIGS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--no-cpu-baseline", *extra]
+        t0 = time.perf_counter()
+        try:
+            res = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+            if res.returncode != 0 or not lines:
+                out[name] = {"error": f"exit {res.returncode}: {res.stderr.strip()[-300:]}"}
+                continue
+            d = json.loads(lines[-1])
+        except (subprocess.SubprocessError, OSError, ValueError) as e:
+            out[name] = {"error": str(e)[:300]}
+            continue
+        keep = {k: d[k] for k in ("value", "unit", "ms_per_step", "steps", "latency_ms", "e2e",
+                                  "one_at_a_time", "runs", "max_diff_over_tol_vs_alone",
+                                  "mode", "clocks") if k in d}
+        if "roofline" in d:
+            r = d["roofline"]
+            keep["roofline"] = {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit",
+                                                        "frac", "traffic", "avg_launch_ms")}
+            if isinstance(r.get("hbm"), dict):
+                keep["roofline"]["hbm_frac"] = r["hbm"].get("frac")
+        keep["config"] = d.get("config", {}).get("workload")
+        keep["wall_s"] = time.perf_counter() - t0
+        out[name] = keep
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -411,7 +459,12 @@ def run_ours(args):
     wl = W.workload(args.workload)
     p, d, t, tol, m = wl["params"], wl["d"], wl["t"], wl["tol"], wl["m"]
     ctx = te.te_create(local)
-    H = te.te_build_model(ctx, p)
+    if p["model"] == "coo":                   # a general matrix handed over as COO triplets
+        rows, cols, vals = W.random_hermitian_coo(p["L"], p["seed"])
+        H = te.te_build_csr(ctx, d, rows, cols, vals)
+        del rows, cols, vals
+    else:
+        H = te.te_build_model(ctx, p)
     te.te_matrix_tune(ctx, H)                 # SpMV work-item size, timed on this GPU
     info = te.te_matrix_info_get(H)
     v0 = W.initial_vector(wl["v0"], d, index_of=lambda occ: te.te_model_basis_index(p, occ))
@@ -520,6 +573,18 @@ def run_ours(args):
         k1_timing = ("CUDA events around the Lanczos step m/2 product of every "
                      "restart inside the timed solves")
 
+    # HBM fraction on the algorithmic bytes of one Lanczos step of the plain CSR method
+    # (complex128 value + int32 column per entry, the row pointer, v_j and v_{j-1} read,
+    # v_{j+1} written: 20 nnz + 4 (d + 1) + 48 d), over the K1 launch and over the whole
+    # solve time per Lanczos step (K1, K2, and the step's share of K3 and K4)
+    b_step = 20 * nnz + 4 * (d + 1) + 48 * d
+    step_s = (elapsed / args.steps) / max(1, stats[0]["matvecs"])
+    csr_step = {"bytes_per_step": b_step, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                "k1_achieved": b_step / k1_avg_s / 1e9, "k1_frac": b_step / k1_avg_s / 1e9 / peaks["hbm_gbs"],
+                "solve_ms_per_step": 1e3 * step_s,
+                "solve_achieved": b_step / step_s / 1e9,
+                "solve_frac": b_step / step_s / 1e9 / peaks["hbm_gbs"]} if not fused else None
+    traffic = (recorded_traffic(K1_SUMMARIES[args.workload]) if args.workload in K1_SUMMARIES else None)
     te.te_matrix_free(H)
     te.te_destroy(ctx)
     if rank == 0:
@@ -535,8 +600,7 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
-                         "traffic": (recorded_traffic(K1_SUMMARIES[args.workload])
-                                     if args.workload in K1_SUMMARIES else None),
+                         "traffic": traffic,
                          "kernel": k1_name,
                          "timing": k1_timing,
                          "value_table": info["sell_dict"],
@@ -549,7 +613,9 @@ def run_ours(args):
                          "attainable": fp64_att,
                          "hbm": {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": achieved / peaks["hbm_gbs"],
-                                 "peak_kind": f"{kind} (MEASURED_PEAKS.json hbm_gbs)"}},
+                                 "peak_kind": f"{kind} (MEASURED_PEAKS.json hbm_gbs)"},
+                         "hbm_csr_step": csr_step,
+                         "dram_overfetch": (traffic / k1_bytes if traffic else None)},
             "spmv_gbs": achieved,
             "solve": {"restarts": restarts[0], "matvecs": stats[0]["matvecs"],
                       "err_bound": stats[0]["err_bound"], "roundoff_est": stats[0]["roundoff_est"],
@@ -561,8 +627,10 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
-        if world == 1 and not args.no_cpu_baseline and wl["params"]["model"] in ("tfim", "xxzdm"):
+        if world == 1 and not args.no_cpu_baseline and wl["params"]["model"] in ("tfim", "xxzdm", "coo"):
             line["cpu_baseline"] = cpu_baseline_entry(wl)
+        if world == 1 and args.workload == WORKLOAD and not args.no_other_configs:
+            line["other_configs"] = other_configs()
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -1177,6 +1245,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="default workload: skip the short runs of the other configurations")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIBE) + ["serve_mix"])
     ap.add_argument("--requests", type=int, default=200, help="serve_mix: requests per load")
     ap.add_argument("--requests-per-load", default="",

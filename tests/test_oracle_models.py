@@ -232,3 +232,22 @@ def test_threaded_product_is_the_plain_product():
     r1 = krylov.evolve(A, W.random_state(72, A.shape[0]), 3.0, 1e-8, 20, threads=1)
     r4 = krylov.evolve(A, W.random_state(72, A.shape[0]), 3.0, 1e-8, 20, threads=4)
     assert np.array_equal(r1.v, r4.v)
+
+
+def test_random_hermitian_coo_is_hermitian_with_distinct_values():
+    """The general-input workload: exactly Hermitian (H[j,i] = conj(H[i,j]) bit for bit),
+    the flip-flop pattern of a periodic chain (L/2 off-diagonal entries per row on
+    average, L + 1 stored per row at most), and one distinct value per coupled pair."""
+    import scipy.sparse
+    L = 10
+    r, c, v = W.random_hermitian_coo(L, 9)
+    d = 1 << L
+    A = models.coo_to_csr(d, r, c, v).to_scipy()
+    D = A - A.getH()
+    assert D.count_nonzero() == 0
+    assert A.nnz == d + L * d // 2
+    assert np.diff(A.indptr).max() <= L + 1
+    off = A.data[A.indices != np.repeat(np.arange(d), np.diff(A.indptr))]
+    upper = off[np.abs(off.imag) > 0]
+    assert np.unique(upper).size == upper.size           # no value repeats
+    assert np.all((np.abs(off) >= 0.5) & (np.abs(off) < 1.0 + 1e-15))

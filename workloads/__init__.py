@@ -18,6 +18,11 @@ workloads, stated once here so both sides read the same words):
   bit i = 0 means up;
 * complex hopping amplitudes are handed over as (re, im) pairs, already formed
   from their random phases here, so the builders multiply and add only.
+
+One workload is a general complex Hermitian matrix given as input data (COO
+triplets with random values on a spin chain's sparsity pattern,
+``random_hermitian_coo``); the CUDA library reads the triplets through
+te_build_csr and the oracle through its own coo_to_csr.
 """
 from __future__ import annotations
 
@@ -33,6 +38,17 @@ _M2 = np.uint64(0x94D049BB133111EB)
 def splitmix64(seed: int, n: int) -> np.ndarray:
     """n outputs of the counter-based splitmix64 stream ``seed`` (uint64)."""
     i = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def splitmix64_at(seed: int, idx: np.ndarray) -> np.ndarray:
+    """Outputs number idx (uint64 array) of the splitmix64 stream ``seed``."""
+    i = np.asarray(idx, dtype=np.uint64) + np.uint64(1)
     with np.errstate(over="ignore"):
         z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
         z = (z ^ (z >> np.uint64(30))) * _M1
@@ -147,6 +163,11 @@ def workload(name: str) -> dict:
         occ = tuple([1] * 10 + [0] * 4)
         return {"name": name, "params": p, "d": bose_dim(14, 10), "v0": ("occupation", occ),
                 "t": 20.0, "m": 50, "tol": 1e-10}
+    if name == "random_L20":
+        # a general complex128 Hermitian matrix given as COO (one distinct value per
+        # coupled pair: ~5.2M values, far above the 65,535 the value-indexed copy takes)
+        return {"name": name, "params": {"model": "coo", "L": 20, "seed": 9}, "d": 1 << 20,
+                "v0": ("random", 309), "t": 50.0, "m": 40, "tol": 1e-8}
     if name == "batch_xxzdm_L20_x64":
         # 64 random initial vectors under the Hamiltonian of xxzdm_L20
         p = xxzdm_params(20, seed=3)
@@ -188,6 +209,39 @@ def workload(name: str) -> dict:
 def initial_block(seeds, d: int) -> np.ndarray:
     """len(seeds) x d block of normalised random states, one row per seed."""
     return np.stack([random_state(s, d) for s in seeds])
+
+
+def random_hermitian_coo(L: int, seed: int):
+    """COO triplets (rows, cols, vals) of a random complex Hermitian matrix of
+    dimension 2^L with the sparsity pattern of a periodic spin-1/2 chain with
+    nearest-neighbour flip-flop terms: entry (r, r ^ (1 << b | 1 << b+1)) for every
+    bond b whose two bits in r differ, and the diagonal.  Every off-diagonal pair
+    draws its own value (so there are as many distinct values as pairs):
+    H[lo, hi] = 1/2 (1 + u) e^{2 pi i v} for the pair lo < hi on bond b, with u, v
+    the uniforms number 2 (lo L + b) and 2 (lo L + b) + 1 of stream ``seed``, and
+    H[hi, lo] = conj(H[lo, hi]); the diagonal entries are U[-1, 1) (stream
+    seed + 1).  Rows come out unsorted; duplicates do not occur."""
+    d = 1 << L
+    r = np.arange(d, dtype=np.int64)
+    rows, cols, vals = [r], [r], [(2.0 * uniform(seed + 1, d) - 1.0).astype(np.complex128)]
+    for b in range(L):
+        c = (b + 1) % L
+        flip = ((r >> b) & 1) != ((r >> c) & 1)
+        src = r[flip]
+        dst = src ^ ((1 << b) | (1 << c))
+        lo = np.minimum(src, dst)
+        key = (lo * L + b).astype(np.uint64)
+        u = (splitmix64_at(seed, 2 * key) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        v = (splitmix64_at(seed, 2 * key + 1) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        mag = 0.5 * (1.0 + u)
+        val = np.empty(src.size, dtype=np.complex128)
+        val.real = mag * np.cos(2.0 * np.pi * v)
+        val.imag = mag * np.sin(2.0 * np.pi * v)
+        val = np.where(src == lo, val, np.conj(val))
+        rows.append(src)
+        cols.append(dst)
+        vals.append(val)
+    return np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
 
 
 def initial_vector(spec, d: int, index_of=None) -> np.ndarray:
