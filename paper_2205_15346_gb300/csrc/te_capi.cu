@@ -561,7 +561,7 @@ te_status te_create_with_allocator(te_ctx** out, int32_t device, void* cuda_stre
     }
     cudaMemset(c->spmv_st, 0, sizeof(DevState));
     if (step_prepare() != cudaSuccess || block_prepare() != cudaSuccess ||
-        sample_prepare() != cudaSuccess) {
+        sample_prepare() != cudaSuccess || sell_prepare() != cudaSuccess) {
         te_destroy(c);
         return TE_ERR_CUDA;
     }
@@ -771,6 +771,7 @@ te_status te_matrix_info_get(const te_matrix* H, te_matrix_info* info) {
     info->sell_dict = H->dict_n;
     info->sell_tpt = H->sell_tpt;
     info->sell_real = H->dict_real ? 1 : 0;
+    info->sell_async = H->sell_async;
     return TE_OK;
 }
 
@@ -813,29 +814,52 @@ void te_matrix_free(te_matrix* H) {
     delete H;
 }
 
+// Cached plans size their scratch for the current SpMV item size and capture its
+// kernel: drop those of H before the product's configuration changes.
+static te_status drop_matrix_plans(te_ctx* ctx, const te_matrix* H) {
+    if (multi_plans_in_use(ctx, H->id))
+        return set_error(ctx, TE_ERR_INVALID_ARG, "a grouped solve on this matrix is running");
+    std::vector<Plan*> drop;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (Plan* p : ctx->plans)
+            if (p->matrix_id == H->id && p->in_use)
+                return set_error(ctx, TE_ERR_INVALID_ARG, "a solve on this matrix is running");
+        auto it = std::partition(ctx->plans.begin(), ctx->plans.end(),
+                                 [&](Plan* p) { return p->matrix_id != H->id; });
+        drop.assign(it, ctx->plans.end());
+        ctx->plans.erase(it, ctx->plans.end());
+    }
+    cudaStreamSynchronize(ctx->stream);
+    for (Plan* p : drop) free_plan(p);
+    multi_plans_release(ctx, H->id);
+    return TE_OK;
+}
+
+te_status te_matrix_set_sell(te_ctx* ctx, te_matrix* H, int32_t slices_per_task, int32_t async_trip) {
+    if (!ctx || !H || slices_per_task < 1 || slices_per_task > 8 ||
+        (async_trip != 0 && async_trip != 2 && async_trip != 4))
+        return TE_ERR_INVALID_ARG;
+    enter(ctx);
+    if (!H->sell_off) return set_error(ctx, TE_ERR_INVALID_ARG, "the matrix has no sliced copy");
+    if (async_trip && !(H->sell_idx && !H->dict_real))
+        return set_error(ctx, TE_ERR_INVALID_ARG,
+                         "staged gathers exist for the complex value-indexed copy only");
+    if (te_status js = join_user_stream(ctx)) return js;
+    if (te_status ds = drop_matrix_plans(ctx, H)) return ds;
+    H->sell_tpt = slices_per_task;
+    H->sell_async = async_trip;
+    H->sell_grid = async_trip ? sell_async_grid(H->nslices, ctx->num_sms, async_trip)
+                              : sell_grid(H->nslices, ctx->num_sms,
+                                          H->sell_idx ? (H->dict_real ? 2 : 1) : 0);
+    return TE_OK;
+}
+
 te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* best_ms) {
     if (!ctx || !H || repeats < 1 || repeats > 100) return TE_ERR_INVALID_ARG;
     enter(ctx);
     if (te_status js = join_user_stream(ctx)) return js;
-    // cached plans size their scratch for the current item size: drop them first
-    if (multi_plans_in_use(ctx, H->id))
-        return set_error(ctx, TE_ERR_INVALID_ARG, "a grouped solve on this matrix is running");
-    {
-        std::vector<Plan*> drop;
-        {
-            std::lock_guard<std::mutex> lk(ctx->mu);
-            for (Plan* p : ctx->plans)
-                if (p->matrix_id == H->id && p->in_use)
-                    return set_error(ctx, TE_ERR_INVALID_ARG, "a solve on this matrix is running");
-            auto it = std::partition(ctx->plans.begin(), ctx->plans.end(),
-                                     [&](Plan* p) { return p->matrix_id != H->id; });
-            drop.assign(it, ctx->plans.end());
-            ctx->plans.erase(it, ctx->plans.end());
-        }
-        cudaStreamSynchronize(ctx->stream);
-        for (Plan* p : drop) free_plan(p);
-        multi_plans_release(ctx, H->id);
-    }
+    if (te_status ds = drop_matrix_plans(ctx, H)) return ds;
     cudaStream_t s = ctx->stream;
     const int64_t d = H->d;
     const int cand[] = {1, 2, 3, 4, 6, 8};
@@ -855,26 +879,41 @@ te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* bes
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = INFINITY;
     int best_tpt = keep;
-    for (int c : cand) {
-        if (e != cudaSuccess) break;
-        if (c > 1 && (H->nslices + c - 1) / c < 4) break;     // too few items to matter
-        H->sell_tpt = c;
-        double tmin = INFINITY;
-        for (int r = 0; r <= repeats && e == cudaSuccess; ++r) {
-            e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) e = launch_spmv_sell(H, x, xsum, nullptr, y, ctx->spmv_st, 0, 1, parts, s);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e == cudaSuccess && r > 0) tmin = std::min(tmin, (double)ms);   // r = 0 warms up
-        }
-        if (e == cudaSuccess && tmin < best) {
-            best = tmin;
-            best_tpt = c;
+    const int keep_async = H->sell_async, keep_grid = H->sell_grid;
+    int best_async = keep_async, best_grid = keep_grid;
+    const int form = H->sell_idx ? (H->dict_real ? 2 : 1) : 0;
+    const int plain_grid = sell_grid(H->nslices, ctx->num_sms, form);
+    // the staged-gather product exists for the complex value table only
+    const int nasync = form == 1 ? 3 : 1;
+    const int asyncs[3] = {0, 2, 4};
+    for (int ai = 0; ai < nasync && e == cudaSuccess; ++ai) {
+        H->sell_async = asyncs[ai];
+        H->sell_grid = asyncs[ai] ? sell_async_grid(H->nslices, ctx->num_sms, asyncs[ai]) : plain_grid;
+        for (int c : cand) {
+            if (e != cudaSuccess) break;
+            if (c > 1 && (H->nslices + c - 1) / c < 4) break;     // too few items to matter
+            H->sell_tpt = c;
+            double tmin = INFINITY;
+            for (int r = 0; r <= repeats && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = launch_spmv_sell(H, x, xsum, nullptr, y, ctx->spmv_st, 0, 1, parts, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && r > 0) tmin = std::min(tmin, (double)ms);   // r = 0 warms up
+            }
+            if (e == cudaSuccess && tmin < best) {
+                best = tmin;
+                best_tpt = c;
+                best_async = H->sell_async;
+                best_grid = H->sell_grid;
+            }
         }
     }
     H->sell_tpt = (e == cudaSuccess) ? best_tpt : keep;
+    H->sell_async = (e == cudaSuccess) ? best_async : keep_async;
+    H->sell_grid = (e == cudaSuccess) ? best_grid : keep_grid;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     dev_free(ctx, x);

@@ -119,6 +119,8 @@ struct te_matrix {
     int64_t sell_nnz = 0;        // stored entries including padding
     int sell_grid = 0;           // blocks of the SpMV grid (resident on all SMs at once)
     int sell_tpt = 1;            // slices per SpMV task (about 1.5K stored entries)
+    int sell_async = 0;          // complex value table: gathers staged in shared memory, 2 or 4
+                                 // entries per trip (0: through registers); set by te_matrix_tune
     // 3M form for the batched product (te_block.cu), built on first use:
     // m3[k] = a, m3[nnz + k] = b - a, m3[2 nnz + k] = a + b for val[k] = a + ib
     double* m3 = nullptr;
@@ -248,6 +250,8 @@ cudaError_t step_prepare();
 // SELL form (te_sell.cu)
 te_status build_sell(te_ctx* ctx, te_matrix* H);
 int sell_grid(int64_t nslices, int num_sms, int form);   // 0 full, 1 indexed, 2 real indexed
+int sell_async_grid(int64_t nslices, int num_sms, int trip);   // the staged indexed product
+cudaError_t sell_prepare();                     // shared-memory limit of the staged product
 int64_t sell_partials(const te_matrix* H);
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,

@@ -352,13 +352,13 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
 // per-group counter tells it) adds the group's partials in task order; the last
 // CTA to finish adds the group sums in group order.  The result does not depend
 // on which warp took which task.
-template <class Slices>
+template <class Slices, int kAsync = 0>
 __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* __restrict__ x,
                                                const double* __restrict__ xs,
                                                const double2* __restrict__ xprev,
                                                double2* __restrict__ y, int64_t d, int64_t nslices,
                                                int tpt, DevState* st, int j, int mode,
-                                               double* partials) {
+                                               double* partials, unsigned char* stage = nullptr) {
     __shared__ double sh[32];
     __shared__ bool am_last;
     double cx = 1.0, bp = 0.0;
@@ -387,7 +387,14 @@ __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* _
             const int64_t row = s * 32 + lane;
             const bool real_row = row < d;
             const double2 xr = real_row ? __ldg(x + row) : make_double2(0.0, 0.0);
-            const double2 hx = M.row(s, lane, x, xs, real_row ? row : -1, xr);
+            double2 hx;
+            if constexpr (kAsync > 0) {
+                const te_slices::Staging<kAsync, 3> stg(
+                    stage + (threadIdx.x >> 5) * te_slices::Staging<kAsync, 3>::kBytesPerWarp);
+                hx = M.template row_async<kAsync>(s, lane, x, xs, real_row ? row : -1, xr, stg);
+            } else {
+                hx = M.row(s, lane, x, xs, real_row ? row : -1, xr);
+            }
             if (real_row) {
                 double2 out = make_double2(cx * hx.x, cx * hx.y);
                 if (bp != 0.0) {
@@ -463,6 +470,21 @@ __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sellv(
     const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
     int tpt, DevState* st, int j, int mode, double* partials) {
     spmv_sell_body(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
+}
+
+// The value-indexed product with its gathers staged through shared memory (te_slices.cuh
+// row_async; kTrip entries per trip, three stages per warp).  The sums are the same as
+// k_spmv_sellv's, added in the same order: the results are bitwise equal.
+// (Four-entry trips take 72 KB of staging per block, so three blocks fit an SM and each
+// thread may use up to 85 registers.)
+template <int kTrip>
+__global__ void __launch_bounds__(TE_BLOCK, kTrip == 4 ? 3 : 4) k_spmv_sellv_async(
+    IndexedSlices M, const double2* __restrict__ x, const double* __restrict__ xs,
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    int tpt, DevState* st, int j, int mode, double* partials) {
+    extern __shared__ __align__(16) unsigned char stage_smem[];
+    spmv_sell_body<IndexedSlices, kTrip>(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials,
+                                         stage_smem);
 }
 
 __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sellr(
@@ -625,6 +647,32 @@ int sell_grid(int64_t nslices, int num_sms, int form) {
     return (int)std::max<int64_t>(1, std::min(need, full));
 }
 
+constexpr int async_smem(int trip) {
+    return (TE_BLOCK / 32) * (trip == 4 ? te_slices::Staging<4, 3>::kBytesPerWarp
+                                        : te_slices::Staging<2, 3>::kBytesPerWarp);
+}
+
+cudaError_t sell_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_spmv_sellv_async<4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, async_smem(4));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_sellv_async<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 async_smem(2));
+    return e;
+}
+
+int sell_async_grid(int64_t nslices, int num_sms, int trip) {
+    int nb = 0;
+    if (trip == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv_async<4>, TE_BLOCK, async_smem(4));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv_async<2>, TE_BLOCK, async_smem(2));
+    if (nb < 1) nb = 1;
+    const int64_t need = (nslices + (TE_BLOCK / 32) - 1) / (TE_BLOCK / 32);
+    const int64_t full = (int64_t)nb * num_sms;
+    return (int)std::max<int64_t>(1, std::min(need, full));
+}
+
 // partials must hold sell_partials(H) doubles (one per chunk of slices); xs holds
 // Re x + Im x.
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
@@ -637,8 +685,15 @@ cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double*
     } else if (H->sell_idx) {
         const IndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->dict_pq,
                               H->sell_diag};
-        k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
-                                                      H->sell_tpt, st, j, mode, partials);
+        if (H->sell_async == 4)
+            k_spmv_sellv_async<4><<<H->sell_grid, TE_BLOCK, async_smem(4), s>>>(
+                M, x, xs, xprev, y, H->d, H->nslices, H->sell_tpt, st, j, mode, partials);
+        else if (H->sell_async == 2)
+            k_spmv_sellv_async<2><<<H->sell_grid, TE_BLOCK, async_smem(2), s>>>(
+                M, x, xs, xprev, y, H->d, H->nslices, H->sell_tpt, st, j, mode, partials);
+        else
+            k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+                                                          H->sell_tpt, st, j, mode, partials);
     } else {
         const FullSlices M{H->sell_off, H->sell_col, H->sell_a, H->sell_pq};
         k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,

@@ -27,6 +27,37 @@ __device__ __forceinline__ T ldm(const T* p) {
     else return __ldcs(p);
 }
 
+// Asynchronous copies global -> shared (cp.async, sm_80 and later): the gathered
+// vector elements of a later trip are in flight without holding registers.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared staging of one warp for the asynchronous row products: kStages trips of
+// kTrip entries, each lane its own slots (x at sx[(stage * kTrip + u) * 32 + lane],
+// x + y at ss[...]).  Bytes per warp: kStages * kTrip * 32 * 24.
+template <int kTrip, int kStages>
+struct Staging {
+    static constexpr int kBytesPerWarp = kStages * kTrip * 32 * 24;
+    double2* sx;
+    double* ss;
+    __device__ __forceinline__ Staging(unsigned char* warp_base)
+        : sx(reinterpret_cast<double2*>(warp_base)),
+          ss(reinterpret_cast<double*>(warp_base + kStages * kTrip * 32 * 16)) {}
+};
+
 // Slice products of the two stored forms.  row() returns, for the lane's row of
 // slice s, the sums k1 = sum a (x + y), k2 = sum (b - a) x, k3 = sum (a + b) y
 // over its stored entries, combined as (k1 - k3, k1 + k2), plus the diagonal
@@ -141,6 +172,94 @@ struct IndexedSlices {
             k3 = fma(p0.y, x0.y, k3);
         }
         const double dg = r >= 0 ? ldm<kL2>(diag + r) : 0.0;
+        return make_double2(fma(dg, xr.x, k1 - k3), fma(dg, xr.y, k1 + k2));
+    }
+
+    // The same row product (same sums, same order) with the gathers of x and x + y
+    // software-pipelined: the column and table indices are loaded two trips ahead into
+    // registers, the gathers of the next trip go to the warp's shared staging by
+    // cp.async while the FMAs of this trip run, so a warp never waits for its own
+    // gathers.  Three stages: a stage is refilled one full trip after it was read.
+    template <int kTrip>
+    __device__ __forceinline__ double2 row_async(int64_t s, int lane, const double2* __restrict__ x,
+                                                 const double* __restrict__ xs, int64_t r,
+                                                 double2 xr, Staging<kTrip, 3> st) const {
+        const int32_t o = __ldg(off + s);
+        const int w = (__ldg(off + s + 1) - o) >> 5;
+        const uint16_t* ip = vidx + o + lane;
+        const int32_t* cp = col + o + lane;
+        double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        const int nt = w / kTrip;                        // full trips
+        int qc[kTrip], q1[kTrip], c1[kTrip];
+        if (nt > 0) {
+#pragma unroll
+            for (int u = 0; u < kTrip; ++u) {            // trip 0: indices, then its gathers
+                const int c0 = __ldcs(cp + 32 * u);
+                qc[u] = __ldcs(ip + 32 * u);
+                cp_async16(st.sx + u * 32 + lane, x + c0);
+                cp_async8(st.ss + u * 32 + lane, xs + c0);
+            }
+            cp_async_commit();
+            if (nt > 1) {
+#pragma unroll
+                for (int u = 0; u < kTrip; ++u) {        // trip 1: indices only
+                    c1[u] = __ldcs(cp + 32 * (kTrip + u));
+                    q1[u] = __ldcs(ip + 32 * (kTrip + u));
+                }
+            }
+        }
+#pragma unroll 1
+        for (int t = 0; t < nt; ++t) {
+            int q2[kTrip], c2[kTrip];
+            if (t + 2 < nt) {                            // indices of trip t + 2
+#pragma unroll
+                for (int u = 0; u < kTrip; ++u) {
+                    c2[u] = __ldcs(cp + 32 * ((t + 2) * kTrip + u));
+                    q2[u] = __ldcs(ip + 32 * ((t + 2) * kTrip + u));
+                }
+            }
+            if (t + 1 < nt) {                            // gathers of trip t + 1
+                const int sg = (t + 1) % 3;
+#pragma unroll
+                for (int u = 0; u < kTrip; ++u) {
+                    cp_async16(st.sx + (sg * kTrip + u) * 32 + lane, x + c1[u]);
+                    cp_async8(st.ss + (sg * kTrip + u) * 32 + lane, xs + c1[u]);
+                }
+            }
+            cp_async_commit();
+            cp_async_wait<1>();                          // trip t has landed
+            const int sc = t % 3;
+#pragma unroll
+            for (int u = 0; u < kTrip; ++u) {
+                const double a = __ldg(ta + qc[u]);
+                const double2 p = __ldg(tpq + qc[u]);
+                const double2 xv = st.sx[(sc * kTrip + u) * 32 + lane];
+                const double z = st.ss[(sc * kTrip + u) * 32 + lane];
+                k1 = fma(a, z, k1);
+                k2 = fma(p.x, xv.x, k2);
+                k3 = fma(p.y, xv.y, k3);
+            }
+#pragma unroll
+            for (int u = 0; u < kTrip; ++u) {
+                qc[u] = q1[u];
+                q1[u] = q2[u];
+                c1[u] = c2[u];
+            }
+        }
+        cp_async_wait<0>();
+#pragma unroll 1
+        for (int k = nt * kTrip; k < w; ++k) {
+            const int qq = __ldcs(ip + 32 * k);
+            const int cc = __ldcs(cp + 32 * k);
+            const double a0 = __ldg(ta + qq);
+            const double2 p0 = __ldg(tpq + qq);
+            const double2 x0 = __ldg(x + cc);
+            const double z0 = __ldg(xs + cc);
+            k1 = fma(a0, z0, k1);
+            k2 = fma(p0.x, x0.x, k2);
+            k3 = fma(p0.y, x0.y, k3);
+        }
+        const double dg = r >= 0 ? __ldcs(diag + r) : 0.0;
         return make_double2(fma(dg, xr.x, k1 - k3), fma(dg, xr.y, k1 + k2));
     }
 };

@@ -83,7 +83,7 @@ class te_matrix_info(C.Structure):
     _fields_ = [("d", C.c_int64), ("nnz", C.c_int64), ("norm1", C.c_double),
                 ("max_row_nnz", C.c_int32), ("spmv_lanes", C.c_int32), ("sell_nnz", C.c_int64),
                 ("sell_dict", C.c_int32), ("sell_tpt", C.c_int32),
-                ("sell_real", C.c_int32)]
+                ("sell_real", C.c_int32), ("sell_async", C.c_int32)]
 
 
 class te_model_desc(C.Structure):
@@ -126,6 +126,7 @@ _SIGS = {
     "te_matrix_free": (None, [_P]),
     "te_matrix_tune": (C.c_int32, [_P, _P, C.c_int32, C.POINTER(C.c_double)]),
     "te_measure_fp64": (C.c_int32, [_P, C.POINTER(C.c_double)]),
+    "te_matrix_set_sell": (C.c_int32, [_P, _P, C.c_int32, C.c_int32]),
     "te_fused_barrier_check": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_int32),
                                            C.POINTER(C.c_double)]),
     "te_spmv": (C.c_int32, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_uint32]),
@@ -403,6 +404,11 @@ def te_matrix_tune(ctx, H, repeats: int = 5) -> float:
     best = C.c_double()
     _check(ctx, lib().te_matrix_tune(ctx, H, int(repeats), C.byref(best)))
     return best.value
+
+
+def te_matrix_set_sell(ctx, H, slices_per_task: int, async_trip: int = 0) -> None:
+    """Pin the sliced SpMV's work-item size and gather staging (0, 2 or 4)."""
+    _check(ctx, lib().te_matrix_set_sell(ctx, H, int(slices_per_task), int(async_trip)))
 
 
 def te_measure_fp64(ctx) -> float:

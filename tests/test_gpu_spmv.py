@@ -175,3 +175,50 @@ def test_measure_fp64_rate_is_within_the_pipe_peak(te, ctx):
     peak = sms * 2 * 2 * mhz * 1e6 / 1e12
     r = te.te_measure_fp64(ctx)
     assert 0.3 * peak < r <= 1.02 * peak, (r, peak)
+
+
+@pytest.mark.parametrize("params", [W.xxzdm_params(14, 2), W.bose_params(10, 6, 4),
+                                    W.xxzdm_params(5, 6)],
+                         ids=["xxzdm14", "bose10_6", "xxzdm5"])
+def test_staged_gather_variants_are_bitwise_the_same_product(te, ctx, params):
+    """The value-indexed product with its gathers staged in shared memory two or
+    four entries ahead (cp.async), for every work-item size: bitwise the product of
+    the register-gather kernel, and within 1e-14 (|A||x|)_i of the oracle's.  Rows
+    of the bosons (17..79 entries) and the tiny chain (w < 4) cover ragged trips."""
+    H = te.te_build_model(ctx, params)
+    try:
+        assert te.te_matrix_info_get(H)["sell_dict"] > 0
+        A = models.build(params).to_scipy()
+        te.te_matrix_set_sell(ctx, H, 1, 0)
+        base = check_spmv(te, ctx, H, A, 13)
+        for tpt in (1, 2, 3, 4, 8):
+            for trip in (0, 2, 4):
+                te.te_matrix_set_sell(ctx, H, tpt, trip)
+                assert te.te_matrix_info_get(H)["sell_async"] == trip
+                y = check_spmv(te, ctx, H, A, 13)
+                assert np.array_equal(y, base), (tpt, trip)
+        # a solve on each staging: bitwise the same state
+        v0 = W.random_state(14, A.shape[0])
+        outs = []
+        for trip in (0, 2, 4):
+            te.te_matrix_set_sell(ctx, H, 2, trip)
+            out, st, _ = te.te_evolve(ctx, H, v0, 3.0, 1e-8, 30, te.make_options(fused_lanczos=1))
+            outs.append(out)
+        assert all(np.array_equal(o, outs[0]) for o in outs)
+        te.te_matrix_tune(ctx, H)                     # the tuner may pick any of them
+        assert te.te_matrix_info_get(H)["sell_async"] in (0, 2, 4)
+        assert np.array_equal(check_spmv(te, ctx, H, A, 13), base)
+    finally:
+        te.te_matrix_free(H)
+
+
+def test_set_sell_rejects_staging_for_other_forms(te, ctx):
+    H = te.te_build_model(ctx, W.tfim_params(8, 1))      # real value table
+    try:
+        with pytest.raises(te.TEError):
+            te.te_matrix_set_sell(ctx, H, 1, 2)
+        with pytest.raises(te.TEError):
+            te.te_matrix_set_sell(ctx, H, 9, 0)
+        te.te_matrix_set_sell(ctx, H, 2, 0)
+    finally:
+        te.te_matrix_free(H)
