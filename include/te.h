@@ -148,8 +148,9 @@ typedef struct te_matrix_info {
                                   zero imaginary part): the product then takes 2 DFMA per entry
                                   instead of 3 */
     int32_t sell_async;        /* complex value table: 0 when the product gathers x through
-                                  registers; 2 or 4 when it stages the gathers of the next trip
-                                  of that many entries in shared memory (cp.async); chosen by
+                                  registers one slice at a time; 1 when it takes two slices per
+                                  pass; 2 or 4 when it stages the gathers of the next trip of
+                                  that many entries in shared memory (cp.async); chosen by
                                   te_matrix_tune, bitwise the same result */
 } te_matrix_info;
 
@@ -277,8 +278,9 @@ void te_matrix_free(te_matrix* H);
 
 /* Autotune the sliced SpMV of H on this GPU: times the product (CUDA events, the
  * best of `repeats` launches after one warm-up) for work items of 1, 2, 3, 4, 6 and
- * 8 slices, and for a complex value table also with the gathers staged in shared
- * memory two or four entries ahead, and keeps the fastest (te_matrix_info.sell_tpt,
+ * 8 slices, and for a complex value table also with two slices per pass and with
+ * the gathers staged in shared memory two or four entries ahead, and keeps the
+ * fastest (te_matrix_info.sell_tpt,
  * sell_async; every candidate gives bitwise the same product).  The initial choice
  * is a fixed rule (about 1.5K stored entries per item, at most 4 slices).  Cached
  * solver plans of H are dropped (their scratch depends on the item size); returns
@@ -287,8 +289,9 @@ void te_matrix_free(te_matrix* H);
 te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* best_ms);
 
 /* Pin the sliced SpMV configuration that te_matrix_tune would choose:
- * slices_per_task 1..8, async_trip 0 (gathers through registers) or 2 / 4 (gathers
- * staged in shared memory that many entries ahead; complex value table only).
+ * slices_per_task 1..8, async_trip 0 (gathers through registers), 1 (two slices
+ * per pass) or 2 / 4 (gathers staged in shared memory that many entries ahead);
+ * 1, 2 and 4 exist for the complex value table only.
  * Every configuration gives bitwise the same product.  Cached plans of H are
  * dropped.  Errors: TE_ERR_INVALID_ARG (bad value, no sliced copy, staging asked
  * for another form, a solve on H running). */

@@ -838,7 +838,7 @@ static te_status drop_matrix_plans(te_ctx* ctx, const te_matrix* H) {
 
 te_status te_matrix_set_sell(te_ctx* ctx, te_matrix* H, int32_t slices_per_task, int32_t async_trip) {
     if (!ctx || !H || slices_per_task < 1 || slices_per_task > 8 ||
-        (async_trip != 0 && async_trip != 2 && async_trip != 4))
+        (async_trip != 0 && async_trip != 1 && async_trip != 2 && async_trip != 4))
         return TE_ERR_INVALID_ARG;
     enter(ctx);
     if (!H->sell_off) return set_error(ctx, TE_ERR_INVALID_ARG, "the matrix has no sliced copy");
@@ -884,8 +884,8 @@ te_status te_matrix_tune(te_ctx* ctx, te_matrix* H, int32_t repeats, double* bes
     const int form = H->sell_idx ? (H->dict_real ? 2 : 1) : 0;
     const int plain_grid = sell_grid(H->nslices, ctx->num_sms, form);
     // the staged-gather product exists for the complex value table only
-    const int nasync = form == 1 ? 3 : 1;
-    const int asyncs[3] = {0, 2, 4};
+    const int nasync = form == 1 ? 4 : 1;
+    const int asyncs[4] = {0, 1, 2, 4};
     for (int ai = 0; ai < nasync && e == cudaSuccess; ++ai) {
         H->sell_async = asyncs[ai];
         H->sell_grid = asyncs[ai] ? sell_async_grid(H->nslices, ctx->num_sms, asyncs[ai]) : plain_grid;

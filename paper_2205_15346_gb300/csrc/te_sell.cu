@@ -352,7 +352,7 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
 // per-group counter tells it) adds the group's partials in task order; the last
 // CTA to finish adds the group sums in group order.  The result does not depend
 // on which warp took which task.
-template <class Slices, int kAsync = 0>
+template <class Slices, int kAsync = 0, bool kPair = false>
 __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* __restrict__ x,
                                                const double* __restrict__ xs,
                                                const double2* __restrict__ xprev,
@@ -382,19 +382,8 @@ __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* _
         const int64_t s0 = big ? (int64_t)c * tpt : nbig * tpt + ((int64_t)c - nbig);
         const int64_t s1 = big ? s0 + tpt : s0 + 1;
         double acc = 0.0;
-#pragma unroll 1
-        for (int64_t s = s0; s < s1; ++s) {
-            const int64_t row = s * 32 + lane;
-            const bool real_row = row < d;
-            const double2 xr = real_row ? __ldg(x + row) : make_double2(0.0, 0.0);
-            double2 hx;
-            if constexpr (kAsync > 0) {
-                const te_slices::Staging<kAsync, 3> stg(
-                    stage + (threadIdx.x >> 5) * te_slices::Staging<kAsync, 3>::kBytesPerWarp);
-                hx = M.template row_async<kAsync>(s, lane, x, xs, real_row ? row : -1, xr, stg);
-            } else {
-                hx = M.row(s, lane, x, xs, real_row ? row : -1, xr);
-            }
+        // y of one row from its product hx; the alpha partial in slice order
+        auto finish = [&](int64_t row, bool real_row, double2 xr, double2 hx) {
             if (real_row) {
                 double2 out = make_double2(cx * hx.x, cx * hx.y);
                 if (bp != 0.0) {
@@ -406,6 +395,35 @@ __device__ __forceinline__ void spmv_sell_body(const Slices& M, const double2* _
                 acc = fma(xr.x, out.x, acc);
                 acc = fma(xr.y, out.y, acc);
             }
+        };
+        int64_t s = s0;
+        if constexpr (kPair) {
+#pragma unroll 1
+            for (; s + 1 < s1; s += 2) {                  // two slices per pass
+                const int64_t ra = s * 32 + lane, rb = ra + 32;
+                const bool reala = ra < d, realb = rb < d;
+                const double2 xa = reala ? __ldg(x + ra) : make_double2(0.0, 0.0);
+                const double2 xb = realb ? __ldg(x + rb) : make_double2(0.0, 0.0);
+                double2 ha, hb;
+                M.row_pair(s, s + 1, lane, x, xs, reala ? ra : -1, realb ? rb : -1, xa, xb, &ha, &hb);
+                finish(ra, reala, xa, ha);
+                finish(rb, realb, xb, hb);
+            }
+        }
+#pragma unroll 1
+        for (; s < s1; ++s) {
+            const int64_t row = s * 32 + lane;
+            const bool real_row = row < d;
+            const double2 xr = real_row ? __ldg(x + row) : make_double2(0.0, 0.0);
+            double2 hx;
+            if constexpr (kAsync > 0) {
+                const te_slices::Staging<kAsync, 3> stg(
+                    stage + (threadIdx.x >> 5) * te_slices::Staging<kAsync, 3>::kBytesPerWarp);
+                hx = M.template row_async<kAsync>(s, lane, x, xs, real_row ? row : -1, xr, stg);
+            } else {
+                hx = M.row(s, lane, x, xs, real_row ? row : -1, xr);
+            }
+            finish(row, real_row, xr, hx);
         }
         acc = warp_sum(acc);
         unsigned int done = 0;
@@ -475,6 +493,15 @@ __global__ void __launch_bounds__(TE_BLOCK, 4) k_spmv_sellv(
 // The value-indexed product with its gathers staged through shared memory (te_slices.cuh
 // row_async; kTrip entries per trip, three stages per warp).  The sums are the same as
 // k_spmv_sellv's, added in the same order: the results are bitwise equal.
+// The value-indexed product taking two slices per pass (te_slices.cuh row_pair): twice
+// the independent gathers and FMA chains per lane for short rows; bitwise k_spmv_sellv's.
+__global__ void __launch_bounds__(TE_BLOCK, 3) k_spmv_sellv_pair(
+    IndexedSlices M, const double2* __restrict__ x, const double* __restrict__ xs,
+    const double2* __restrict__ xprev, double2* __restrict__ y, int64_t d, int64_t nslices,
+    int tpt, DevState* st, int j, int mode, double* partials) {
+    spmv_sell_body<IndexedSlices, 0, true>(M, x, xs, xprev, y, d, nslices, tpt, st, j, mode, partials);
+}
+
 // (Four-entry trips take 72 KB of staging per block, so three blocks fit an SM and each
 // thread may use up to 85 registers.)
 template <int kTrip>
@@ -663,7 +690,9 @@ cudaError_t sell_prepare() {
 
 int sell_async_grid(int64_t nslices, int num_sms, int trip) {
     int nb = 0;
-    if (trip == 4)
+    if (trip == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv_pair, TE_BLOCK, 0);
+    else if (trip == 4)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv_async<4>, TE_BLOCK, async_smem(4));
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sellv_async<2>, TE_BLOCK, async_smem(2));
@@ -685,7 +714,10 @@ cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double*
     } else if (H->sell_idx) {
         const IndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->dict_pq,
                               H->sell_diag};
-        if (H->sell_async == 4)
+        if (H->sell_async == 1)
+            k_spmv_sellv_pair<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+                                                               H->sell_tpt, st, j, mode, partials);
+        else if (H->sell_async == 4)
             k_spmv_sellv_async<4><<<H->sell_grid, TE_BLOCK, async_smem(4), s>>>(
                 M, x, xs, xprev, y, H->d, H->nslices, H->sell_tpt, st, j, mode, partials);
         else if (H->sell_async == 2)

@@ -180,6 +180,79 @@ struct IndexedSlices {
     // registers, the gathers of the next trip go to the warp's shared staging by
     // cp.async while the FMAs of this trip run, so a warp never waits for its own
     // gathers.  Three stages: a stage is refilled one full trip after it was read.
+    // The lane's rows of two slices at once (rows r0 of s0 and r1 of s1): over the
+    // entries both rows have, each trip gathers two entries of each, so twice as many
+    // independent loads and FMA chains are in flight per lane; the longer row then
+    // finishes alone.  Each row's sums take its entries in storage order, as row()
+    // does, so the results are bitwise row()'s.
+    __device__ __forceinline__ void row_pair(int64_t s0, int64_t s1, int lane,
+                                             const double2* __restrict__ x,
+                                             const double* __restrict__ xs, int64_t r0, int64_t r1,
+                                             double2 xr0, double2 xr1, double2* h0,
+                                             double2* h1) const {
+        const int32_t o0 = __ldg(off + s0), o1 = __ldg(off + s1);
+        const int w0 = (__ldg(off + s0 + 1) - o0) >> 5;
+        const int w1 = (__ldg(off + s1 + 1) - o1) >> 5;
+        const uint16_t* ip0 = vidx + o0 + lane;
+        const uint16_t* ip1 = vidx + o1 + lane;
+        const int32_t* cp0 = col + o0 + lane;
+        const int32_t* cp1 = col + o1 + lane;
+        double a1 = 0.0, a2 = 0.0, a3 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+        const int wc = w0 < w1 ? w0 : w1;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 2 <= wc; k += 2) {
+            int c[4], q[4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                c[u] = __ldcs(cp0 + 32 * (k + u));
+                q[u] = __ldcs(ip0 + 32 * (k + u));
+                c[2 + u] = __ldcs(cp1 + 32 * (k + u));
+                q[2 + u] = __ldcs(ip1 + 32 * (k + u));
+            }
+            double a[4], z[4];
+            double2 p[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __ldg(ta + q[u]);
+                p[u] = __ldg(tpq + q[u]);
+                xv[u] = __ldg(x + c[u]);
+                z[u] = __ldg(xs + c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                a1 = fma(a[u], z[u], a1);
+                a2 = fma(p[u].x, xv[u].x, a2);
+                a3 = fma(p[u].y, xv[u].y, a3);
+                b1 = fma(a[2 + u], z[2 + u], b1);
+                b2 = fma(p[2 + u].x, xv[2 + u].x, b2);
+                b3 = fma(p[2 + u].y, xv[2 + u].y, b3);
+            }
+        }
+        // the rest of each row alone, in storage order
+        auto rest = [&](const int32_t* cp, const uint16_t* ip, int w, double& k1, double& k2,
+                        double& k3) {
+#pragma unroll 1
+            for (int kk = k; kk < w; ++kk) {
+                const int qq = __ldcs(ip + 32 * kk);
+                const int cc = __ldcs(cp + 32 * kk);
+                const double a0 = __ldg(ta + qq);
+                const double2 p0 = __ldg(tpq + qq);
+                const double2 x0 = __ldg(x + cc);
+                const double z0 = __ldg(xs + cc);
+                k1 = fma(a0, z0, k1);
+                k2 = fma(p0.x, x0.x, k2);
+                k3 = fma(p0.y, x0.y, k3);
+            }
+        };
+        rest(cp0, ip0, w0, a1, a2, a3);
+        rest(cp1, ip1, w1, b1, b2, b3);
+        const double d0 = r0 >= 0 ? __ldcs(diag + r0) : 0.0;
+        const double d1 = r1 >= 0 ? __ldcs(diag + r1) : 0.0;
+        *h0 = make_double2(fma(d0, xr0.x, a1 - a3), fma(d0, xr0.y, a1 + a2));
+        *h1 = make_double2(fma(d1, xr1.x, b1 - b3), fma(d1, xr1.y, b1 + b2));
+    }
+
     template <int kTrip>
     __device__ __forceinline__ double2 row_async(int64_t s, int lane, const double2* __restrict__ x,
                                                  const double* __restrict__ xs, int64_t r,
