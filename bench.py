@@ -1120,7 +1120,7 @@ def run_serve(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     ctx = te.te_create(local)
-    te.te_serve_config(ctx, te.TE_SERVE_BATCH, 40, args.arena, args.large_nnz)
+    te.te_serve_config(ctx, te.TE_SERVE_BATCH, 40, args.arena, args.large_nnz, args.small_nnz)
     m = 40
     pool = []
     for fam, p in W.serve_pool():
@@ -1129,6 +1129,13 @@ def run_serve(args):
         d = te.te_matrix_info_get(H)["d"]
         # four seeded initial states per Hamiltonian; request i takes variant i mod 4
         pool.append((H, d, [W.random_state(600 + 4 * len(pool) + j, d) for j in range(4)]))
+    nnz_of = [te.te_matrix_info_get(H)["nnz"] for H, _, _ in pool]
+
+    def lane_of(k):
+        n = nnz_of[k]
+        if args.large_nnz > 0 and n >= args.large_nnz:
+            return "large"
+        return "small" if n < args.small_nnz else "medium"
     loads = [float(x) for x in args.loads.split(",")]
     counts = ([int(x) for x in args.requests_per_load.split(",")] if args.requests_per_load
               else [args.requests] * len(loads))
@@ -1195,7 +1202,18 @@ def run_serve(args):
                 te.te_request_free(pending.pop(i))
             time.sleep(0.0002)
         span = time.perf_counter() - t0
+        by_lane = {}
+        for lane in ("small", "medium", "large"):
+            idx = [i for i in range(n) if lane_of(reqs[i][0]) == lane]
+            if idx:
+                by_lane[lane] = {"requests": len(idx),
+                                 "served_ms_p50": 1e3 * float(np.percentile(lat[idx], 50)),
+                                 "served_ms_p99": 1e3 * float(np.percentile(lat[idx], 99)),
+                                 "one_at_a_time_ms_p50": 1e3 * float(np.percentile(np.array(lat_solo)[idx], 50)),
+                                 "one_at_a_time_ms_p99": 1e3 * float(np.percentile(np.array(lat_solo)[idx], 99)),
+                                 "service_ms_p50": 1e3 * float(np.percentile(solo_s[idx], 50))}
         runs.append({
+            "by_lane": by_lane,
             "load": load, "requests": n, "arrival_rate_per_s": rate,
             "served": {"solves_per_s": n / span, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                        "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)),
@@ -1207,8 +1225,10 @@ def run_serve(args):
         })
     clk.__exit__(None, None, None)
     head = runs[loads.index(0.8)] if 0.8 in loads else runs[0]
-    lane = (f"large lane (one at a time, solo solve) for nnz >= {args.large_nnz}" if args.large_nnz > 0
-            else "every request batched")
+    lane = ((f"large lane (one at a time, solo solve) for nnz >= {args.large_nnz}" if args.large_nnz > 0
+             else "no large lane") + "; " +
+            (f"small batch for nnz < {args.small_nnz}, medium batch above" if args.small_nnz > 0
+             else "one batch"))
     line = {
         "metric": METRIC, "mode": "serve", "value": head["served"]["solves_per_s"], "unit": "solves/s",
         "n_gpus": 1, "steps": head["requests"], "warmup": len(pool) + len(warm),
@@ -1258,6 +1278,8 @@ def main():
                     help="memory_scaling: also time every size with Gauss-Legendre and tanh-sinh")
     ap.add_argument("--large-nnz", type=int, default=1 << 24,
                     help="serve_mix: large-lane threshold on nnz (negative: batch everything)")
+    ap.add_argument("--small-nnz", type=int, default=1 << 21,
+                    help="serve_mix: small-batch threshold on nnz (negative: one batch)")
     ap.add_argument("--arena", type=int, default=1 << 25,
                     help="serve_mix: elements per Krylov column of the serving arena")
     args = ap.parse_args()

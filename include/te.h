@@ -511,11 +511,13 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
 /* Queue a solve with the same meaning as te_evolve.  v_in is copied before the
  * call returns.  H must outlive the request.  How requests are served
  * (te_serve_config):
- *   TE_SERVE_BATCH (default): continuous batching.  One serving loop per
- *     context keeps the Krylov state of every running request on the device
- *     in an arena of slots and advances all of them together, one restart of
- *     Algorithm 1 per round, through the grouped kernels of te_evolve_multi
- *     (every Lanczos step of all running requests is one launch).  The restart
+ *   TE_SERVE_BATCH (default): continuous batching.  Two serving loops per
+ *     context (small requests, H with fewer than 2^21 stored entries, and
+ *     medium ones, each on a stream of its own) keep the Krylov state of every
+ *     running request on the device in an arena of slots and advance all of
+ *     them together, one restart of Algorithm 1 per round, through the grouped
+ *     kernels of te_evolve_multi (every Lanczos step of all running requests of
+ *     a loop is one launch), so small requests go round in short rounds.  The restart
  *     boundary is the checkpoint: a queued request is admitted, in arrival
  *     order, at the next round boundary as soon as a slot of its size
  *     ((d rounded up to 32) elements of the arena) is free, and a finished
@@ -524,9 +526,9 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
  *     order).  Requests whose H holds at least the large-lane threshold of
  *     stored entries (default 2^24; one restart of such a request fills the
  *     GPU by itself) run in the large lane instead: one at a time, first come
- *     first served, as a solo solve on its own stream beside the batch (that
- *     stream has the highest priority, the batch's the lowest), so that large
- *     requests neither slow each other down nor wait behind small ones.  Requests with reorthogonalisation, the CSR kernel (spmv_lanes),
+ *     first served, as a solo solve on its own stream beside the batches (stream
+ *     priorities: small batch highest, large lane next, medium batch lowest), so
+ *     that large requests neither slow each other down nor wait behind small ones.  Requests with reorthogonalisation, the CSR kernel (spmv_lanes),
  *     TE_OPT_PROFILE, m above the arena depth or d above its capacity take
  *     the large lane too.
  *   TE_SERVE_SOLO: up to 8 worker threads each admit the oldest queued request
@@ -555,15 +557,17 @@ te_status te_set_memory_budget(te_ctx* ctx, int64_t bytes);
 /* How te_submit serves requests.  m_max is the Krylov depth of the serving
  * arena (1..TE_M_MAX; 0: keep, default 40), capacity the number of vector
  * elements per Krylov column it holds (0: keep; default
- * min(2^24, budget / (16 (m_max + 1) + 8)) at first use), and large_nnz the
- * large-lane threshold on the stored entries of H (0: keep, default 2^24;
- * negative: no large lane, every eligible request is batched).  The arena takes
- * (m_max + 1) capacity 16 + capacity 8 bytes once the first batched request
- * arrives, counts against the memory budget, and is released by te_destroy.
+ * min(2^24, budget / (16 (m_max + 1) + 8)) at first use) in the medium batch's
+ * arena (the small batch's holds a quarter of it), large_nnz the large-lane
+ * threshold on the stored entries of H (0: keep, default 2^24; negative: no large
+ * lane) and small_nnz the small batch's (0: keep, default 2^21; negative: one
+ * batch for everything below the large lane).  Each arena takes
+ * (m_max + 1) capacity 16 + capacity 8 bytes once its first request arrives,
+ * counts against the memory budget, and is released by te_destroy.
  * Allowed only while no request is queued or running (else
  * TE_ERR_INVALID_ARG). */
 te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity,
-                          int64_t large_nnz);
+                          int64_t large_nnz, int64_t small_nnz);
 
 #ifdef __cplusplus
 }

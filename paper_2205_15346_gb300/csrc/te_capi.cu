@@ -583,7 +583,8 @@ void te_destroy(te_ctx* ctx) {
     ctx->qcv.notify_all();
     for (auto& t : ctx->workers)
         if (t.joinable()) t.join();
-    if (ctx->batcher.joinable()) ctx->batcher.join();
+    for (auto& b : ctx->batcher)
+        if (b.joinable()) b.join();
     for (Plan* p : ctx->plans) free_plan(p);
     ctx->plans.clear();
     block_plans_release(ctx, 0);
@@ -1166,18 +1167,19 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
 // ------------------------------------------------------------------ requests
 
 te_status te_serve_config(te_ctx* ctx, int32_t mode, int32_t m_max, int64_t capacity,
-                          int64_t large_nnz) {
+                          int64_t large_nnz, int64_t small_nnz) {
     if (!ctx || (mode != TE_SERVE_BATCH && mode != TE_SERVE_SOLO) || m_max < 0 || m_max > TE_M_MAX ||
         capacity < 0)
         return TE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->qmu);
     if (ctx->pending != 0)
         return set_error(ctx, TE_ERR_INVALID_ARG, "te_serve_config: requests are queued or running");
-    if (ctx->batcher.joinable() && (m_max != 0 || capacity != 0))
+    if ((ctx->batcher[0].joinable() || ctx->batcher[1].joinable()) && (m_max != 0 || capacity != 0))
         return set_error(ctx, TE_ERR_INVALID_ARG,
                          "te_serve_config: the serving arena exists; set its shape before the first request");
     ctx->serve_mode = mode;
     if (large_nnz) ctx->serve_large_nnz = large_nnz;
+    if (small_nnz) ctx->serve_small_nnz = std::max<int64_t>(small_nnz, 0);
     if (m_max) ctx->serve_m = m_max;
     if (capacity) ctx->serve_cap = std::max<int64_t>(32, capacity / 32 * 32);
     return TE_OK;
@@ -1229,9 +1231,10 @@ te_status te_submit(te_ctx* ctx, const te_matrix* H, const double* v_in, double 
             ctx->serve_cap = std::max<int64_t>(32, std::min<int64_t>(1ll << 24, ctx->budget / per) / 32 * 32);
         }
         ctx->pending += 1;
-        if (serve_eligible(ctx, r)) {
-            ctx->bqueue.push_back(r);
-            if (!ctx->batcher.joinable()) ctx->batcher = std::thread(serve_loop, ctx);
+        const int cls = serve_class(ctx, r);
+        if (cls >= 0) {
+            ctx->bqueue[cls].push_back(r);
+            if (!ctx->batcher[cls].joinable()) ctx->batcher[cls] = std::thread(serve_loop, ctx, cls);
         } else {
             ctx->queue.push_back(r);
             if ((int)ctx->workers.size() < ctx->max_workers) ctx->workers.emplace_back(worker_loop, ctx);
@@ -1280,7 +1283,7 @@ void te_request_free(te_request* r) {
     bool queued_removed = false;
     if (ctx) {
         std::lock_guard<std::mutex> lk(ctx->qmu);
-        for (auto* q : {&ctx->queue, &ctx->bqueue}) {
+        for (auto* q : {&ctx->queue, &ctx->bqueue[0], &ctx->bqueue[1]}) {
             auto it = std::find(q->begin(), q->end(), r);
             if (it != q->end()) {
                 q->erase(it);
@@ -1309,11 +1312,11 @@ namespace {
 void worker_loop(te_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStream_t s = nullptr;
-    // the highest stream priority: a large-lane solve keeps the SMs it needs while the
-    // batch (lowest priority) takes what is left
+    // a middle stream priority: below the small batch's short kernels, above the medium
+    // batch, so a large-lane solve keeps the SMs it needs against the medium rounds
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
+    cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, (lo + hi) / 2);
     for (;;) {
         te_request* r = nullptr;
         bool counted = false;                 // r's footprint is in ctx->in_use

@@ -203,13 +203,14 @@ struct te_ctx {
     std::condition_variable qcv;
     std::deque<te_request*> queue;   // requests for the solo workers
     std::vector<std::thread> workers;
-    std::deque<te_request*> bqueue;  // requests for the serving loop (continuous batching)
-    std::thread batcher;
+    std::deque<te_request*> bqueue[2];   // requests for the two serving loops (continuous
+    std::thread batcher[2];              // batching): [0] small requests, [1] medium ones
     int serve_mode = TE_SERVE_BATCH;
     int serve_m = 40;                // Krylov depth of the serving arena
     int64_t serve_cap = 0;           // elements per arena column (0: from the budget at first use)
     int64_t pending = 0;             // requests submitted and not yet finished
     int64_t serve_large_nnz = 1ll << 24;   // batch mode: H with this many entries takes the large lane
+    int64_t serve_small_nnz = 1ll << 21;   // batch mode: H with fewer entries joins the small batch
     int solo_running = 0;            // requests the solo workers are running
     bool stopping = false;
     int64_t budget = 0;
@@ -218,8 +219,10 @@ struct te_ctx {
 };
 
 // continuous-batching serving loop (te_multi.cu)
-bool serve_eligible(const te_ctx* ctx, const te_request* r);
-void serve_loop(te_ctx* ctx);
+// -1: the large lane (solo workers); 0: the small batch; 1: the medium batch
+int serve_class(const te_ctx* ctx, const te_request* r);
+int64_t serve_class_capacity(const te_ctx* ctx, int cls);
+void serve_loop(te_ctx* ctx, int cls);
 
 // ---- host launchers (kernels live in te_lanczos.cu, te_step.cu, te_build.cu)
 

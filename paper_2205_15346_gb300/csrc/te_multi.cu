@@ -794,14 +794,15 @@ struct ServeEngine {
     std::vector<std::pair<int64_t, int64_t>> holes;   // free arena segments (offset, length)
     bool dirty = true;              // composition changed since the last capture
 
-    te_status init(te_ctx* c, int m_max, int64_t capacity) {
+    te_status init(te_ctx* c, int m_max, int64_t capacity, int cls) {
         ctx = c;
         depth = m_max;
         cap = capacity / 32 * 32;
         npart = (size_t)(cap / 32 + 2 * TE_MULTI_MAX + 1);
-        int lo = 0, hi = 0;                         // the batch runs at the lowest priority
+        int lo = 0, hi = 0;              // small batch: the highest priority; medium: the lowest
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, lo);
+        const int prio = cls == 0 ? hi : lo;
+        cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio);
         if (e == cudaSuccess) e = dev_alloc(ctx, &V, sizeof(double2) * (size_t)(depth + 1) * (size_t)cap);
         if (e == cudaSuccess) e = dev_alloc(ctx, &S, sizeof(double) * (size_t)cap);
         if (e == cudaSuccess) e = dev_alloc(ctx, &partials, sizeof(double) * npart);
@@ -1013,15 +1014,27 @@ const char* device_status_msg(te_status s) {
 
 }  // namespace
 
-bool serve_eligible(const te_ctx* ctx, const te_request* r) {
-    return ctx->serve_mode == TE_SERVE_BATCH && r->opt.reorth == TE_REORTH_NONE &&
-           r->opt.spmv_lanes == 0 && !(r->opt.flags & TE_OPT_PROFILE) && r->m <= ctx->serve_m &&
-           r->H->sell_off != nullptr && (r->H->d + 31) / 32 * 32 <= ctx->serve_cap &&
-           (ctx->serve_large_nnz <= 0 || r->H->nnz < ctx->serve_large_nnz);
+// The small batch's arena holds a quarter of the medium one's columns.
+int64_t serve_class_capacity(const te_ctx* ctx, int cls) {
+    return cls == 0 ? std::max<int64_t>(32, ctx->serve_cap / 4 / 32 * 32) : ctx->serve_cap;
 }
 
-// The serving loop (one thread per context, started by the first batched request).
-void serve_loop(te_ctx* ctx) {
+int serve_class(const te_ctx* ctx, const te_request* r) {
+    const bool batchable = ctx->serve_mode == TE_SERVE_BATCH && r->opt.reorth == TE_REORTH_NONE &&
+                           r->opt.spmv_lanes == 0 && !(r->opt.flags & TE_OPT_PROFILE) &&
+                           r->m <= ctx->serve_m && r->H->sell_off != nullptr;
+    if (!batchable) return -1;
+    if (ctx->serve_large_nnz > 0 && r->H->nnz >= ctx->serve_large_nnz) return -1;
+    const int64_t seg = (r->H->d + 31) / 32 * 32;
+    if (r->H->nnz < ctx->serve_small_nnz && seg <= serve_class_capacity(ctx, 0)) return 0;
+    return seg <= serve_class_capacity(ctx, 1) ? 1 : -1;
+}
+
+// A serving loop (one thread per context and class, started by the first request of its
+// class).  The small batch's stream has the highest priority (its kernels are short), the
+// large lane's the next and the medium batch's the lowest, so the short rounds of small
+// requests are not held up behind long rounds.
+void serve_loop(te_ctx* ctx, int cls) {
     cudaSetDevice(ctx->device);
     ServeEngine E;
     te_status init_st = TE_OK;
@@ -1030,17 +1043,17 @@ void serve_loop(te_ctx* ctx) {
         std::vector<te_request*> cancelled;
         {
             std::unique_lock<std::mutex> lk(ctx->qmu);
-            ctx->qcv.wait(lk, [&] { return ctx->stopping || !ctx->bqueue.empty() || !E.slots.empty(); });
+            ctx->qcv.wait(lk, [&] { return ctx->stopping || !ctx->bqueue[cls].empty() || !E.slots.empty(); });
             if (ctx->stopping) {
-                for (te_request* r : ctx->bqueue) {
+                for (te_request* r : ctx->bqueue[cls]) {
                     r->state.store(1);
                     cancelled.push_back(r);
                 }
-                ctx->bqueue.clear();
+                ctx->bqueue[cls].clear();
             } else {
                 if (!ready && init_st == TE_OK) {
                     lk.unlock();
-                    init_st = E.init(ctx, ctx->serve_m, ctx->serve_cap);
+                    init_st = E.init(ctx, ctx->serve_m, serve_class_capacity(ctx, cls), cls);
                     lk.lock();
                     if (init_st == TE_OK) {
                         ready = true;
@@ -1048,17 +1061,17 @@ void serve_loop(te_ctx* ctx) {
                     }
                 }
                 if (!ready) {                           // no arena: every queued request fails
-                    for (te_request* r : ctx->bqueue) {
+                    for (te_request* r : ctx->bqueue[cls]) {
                         r->state.store(1);
                         cancelled.push_back(r);
                     }
-                    ctx->bqueue.clear();
+                    ctx->bqueue[cls].clear();
                 }
                 // admission in arrival order while slots and arena space last
-                while (ready && !ctx->bqueue.empty() && (int)E.slots.size() < TE_MULTI_MAX) {
-                    te_request* r = ctx->bqueue.front();
+                while (ready && !ctx->bqueue[cls].empty() && (int)E.slots.size() < TE_MULTI_MAX) {
+                    te_request* r = ctx->bqueue[cls].front();
                     if (r->cancel.load()) {
-                        ctx->bqueue.pop_front();
+                        ctx->bqueue[cls].pop_front();
                         r->state.store(1);
                         cancelled.push_back(r);
                         continue;
@@ -1066,7 +1079,7 @@ void serve_loop(te_ctx* ctx) {
                     const int64_t seg = (r->H->d + 31) / 32 * 32;
                     const int64_t off = E.take(seg);
                     if (off < 0) break;
-                    ctx->bqueue.pop_front();
+                    ctx->bqueue[cls].pop_front();
                     r->state.store(1);
                     ServeSlot sl;
                     sl.r = r;

@@ -152,7 +152,7 @@ _SIGS = {
     "te_cancel": (C.c_int32, [_P]),
     "te_request_free": (None, [_P]),
     "te_set_memory_budget": (C.c_int32, [_P, C.c_int64]),
-    "te_serve_config": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64]),
+    "te_serve_config": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64]),
 }
 
 _lib = None
@@ -730,8 +730,9 @@ def te_set_memory_budget(ctx, nbytes: int) -> None:
 
 
 def te_serve_config(ctx, mode: int = 0, m_max: int = 0, capacity: int = 0,
-                    large_nnz: int = 0) -> None:
+                    large_nnz: int = 0, small_nnz: int = 0) -> None:
     """How te_submit serves requests: TE_SERVE_BATCH (continuous batching) or
-    TE_SERVE_SOLO; m_max / capacity shape the serving arena, large_nnz is the
-    large-lane threshold (0: keep; negative: no large lane)."""
-    _check(ctx, lib().te_serve_config(ctx, int(mode), int(m_max), int(capacity), int(large_nnz)))
+    TE_SERVE_SOLO; m_max / capacity shape the serving arenas, large_nnz is the
+    large-lane threshold and small_nnz the small batch's (0: keep; negative: none)."""
+    _check(ctx, lib().te_serve_config(ctx, int(mode), int(m_max), int(capacity), int(large_nnz),
+                                      int(small_nnz)))
