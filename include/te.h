@@ -60,6 +60,8 @@ typedef int32_t te_status;
 #define TE_WARN_ROUNDOFF     0x1u  /* d ||H||_1 eps exceeded a step's error integral (eq. numericalError, Sec. 2.4) */
 #define TE_WARN_QUAD         0x2u  /* an error integral did not reach quad_rel_tol within quad_max_levels (Sec. 4) */
 #define TE_FLAG_BREAKDOWN    0x4u  /* a lucky breakdown ended a Krylov space early (Sec. 2.4 step 1) */
+#define TE_FLAG_FUSED_RETRY  0x8u  /* a grid barrier of the fused Lanczos loop gave up; that restart
+                                      and the rest of the solve ran as separate launches */
 
 #define TE_M_MAX 128               /* largest Krylov dimension m */
 
@@ -77,6 +79,9 @@ typedef int32_t te_status;
                                       Lanczos steps of a restart as one cooperative kernel (default) */
 #define TE_FUSED_OFF  1            /* always one launch per product and per orthogonalisation */
 /* te_options.flags */
+#define TE_OPT_TEST_FUSED_TIMEOUT 0x20u   /* test aid: one block of the first fused Lanczos loop
+                                           leaves before its first grid barrier, so the others'
+                                           bounded wait (1 s) runs out and the retry path runs */
 #define TE_OPT_PROFILE 0x10u       /* time the fused SpMV of Lanczos step m/2 of every restart with
                                       CUDA events (te_stats.spmv_*; one event pair per restart; with
                                       a fused Lanczos loop the pair brackets that whole kernel) */

@@ -62,6 +62,7 @@ namespace {
 void free_plan(Plan* p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->exec_unfused) cudaGraphExecDestroy(p->exec_unfused);
     if (p->graph) cudaGraphDestroy(p->graph);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     te_ctx* c = p->ctx;
@@ -86,29 +87,34 @@ size_t plan_bytes(int64_t d, int m, int reorth, int max_grid) {
     return b;
 }
 
-// Record one restart of the solve into a graph (see the file comment).
-te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
+// Record one restart of the solve into a graph (see the file comment): with the
+// fused Lanczos loop when `fused`, else as separate launches (a fused plan records
+// both, the second one without profiling events, for the retry after a barrier
+// timeout).
+te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s, bool fused,
+                          cudaGraphExec_t* out) {
     const te_matrix* H = p->H;
     const int64_t d = p->d;
     const int m = p->m;
+    const bool profile = p->profile && fused == (p->fused != 0);
     TE_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    if (p->fused) {
+    if (fused) {
         // the m Lanczos steps as one cooperative kernel (small d), timed as a whole
-        if (p->profile) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
+        if (profile) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
         if (e == cudaSuccess)
             e = launch_lanczos_fused(H, p->V, p->S, p->st, m, p->partials, p->bar, p->fused_grid,
                                      p->fused_threads, s);
-        if (p->profile && e == cudaSuccess)
+        if (profile && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
     }
-    for (int j = 0; j < m && e == cudaSuccess && !p->fused; ++j) {
+    for (int j = 0; j < m && e == cudaSuccess && !fused; ++j) {
         const double2* x = p->V + (size_t)j * d;
         const double2* xprev = j > 0 ? p->V + (size_t)(j - 1) * d : nullptr;
         double2* y = p->V + (size_t)(j + 1) * d;
         double* sj1 = p->S ? p->S + (size_t)(j + 1) * d : nullptr;   // Re + Im of column j + 1
         // external event nodes: plain records inside a capture only order work
-        const bool timed = p->profile && j == m / 2;     // one product per restart is timed
+        const bool timed = profile && j == m / 2;        // one product per restart is timed
         if (timed) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
         if (e == cudaSuccess)
             e = p->lanes ? launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
@@ -146,8 +152,9 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s) {
         return cuda_error(ctx, e, "capturing the restart graph");
     }
     if (e2 != cudaSuccess) return cuda_error(ctx, e2, "cudaStreamEndCapture");
-    p->graph = g;
-    TE_CUDA_TRY(ctx, cudaGraphInstantiate(&p->exec, g, 0));
+    cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return cuda_error(ctx, e3, "cudaGraphInstantiate (restart)");
     return TE_OK;
 }
 
@@ -210,7 +217,8 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
         p->ev.resize(2);
         for (auto& ev : p->ev) cudaEventCreate(&ev);
     }
-    te_status st = capture_restart(ctx, p, s);
+    te_status st = capture_restart(ctx, p, s, fused != 0, &p->exec);
+    if (st == TE_OK && fused) st = capture_restart(ctx, p, s, false, &p->exec_unfused);
     if (st) {
         free_plan(p);
         return st;
@@ -321,6 +329,7 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     ini->quad_max_levels = o.quad_max_levels;
     ini->max_substeps = o.max_substeps;
     ini->smallexp = o.small_exp;
+    ini->test_hold = (o.flags & TE_OPT_TEST_FUSED_TIMEOUT) ? 1 : 0;
     ini->first = 1;
     ini->m_eff = p->m;
     ini->min_err_step = INFINITY;
@@ -350,6 +359,8 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     // eq. numericalError, compared with each step's error integral (Sec. 2.4)
     const double per_restart = (double)d * H->norm1 * 2.220446049250313e-16;
     te_status result = TE_OK;
+    bool unfused = false;          // a fused restart timed out: the rest of the solve runs unfused
+    int64_t fused_restarts = 0;
     if (h->status != 0) {
         result = h->status;
         set_error(ctx, result, result == TE_ERR_NONFINITE ? "v_in has NaN or Inf entries"
@@ -360,9 +371,28 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
                 result = set_error(ctx, TE_ERR_CANCELLED, "request cancelled");
                 break;
             }
-            TE_CUDA_TRY(ctx, cudaGraphLaunch(p->exec, s));
+            const bool fused_now = p->fused && !unfused;
+            DevState before;                   // the state this restart starts from
+            if (fused_now) memcpy(&before, h, sizeof(DevState));
+            TE_CUDA_TRY(ctx, cudaGraphLaunch(fused_now ? p->exec : p->exec_unfused
+                                                       ? p->exec_unfused : p->exec, s));
             TE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-            if (p->profile && (p->fused || p->m / 2 < h->last_m_eff)) {   // the timed work ran
+            if (fused_now && h->status == TE_ERR_TIMEOUT && p->exec_unfused) {
+                // A grid barrier of the fused loop gave up (a block was not scheduled in
+                // time).  The loop writes only columns 1..m of the basis, so column 0 still
+                // holds this restart's start: restore the state and run the restart again
+                // as separate launches, and the rest of the solve that way.
+                before.test_hold = 0;
+                TE_CUDA_TRY(ctx, cudaMemcpyAsync(p->st, &before, sizeof(DevState),
+                                                 cudaMemcpyHostToDevice, s));
+                TE_CUDA_TRY(ctx, cudaMemsetAsync(p->bar, 0, 3 * sizeof(unsigned int), s));
+                unfused = true;
+                S.flags |= TE_FLAG_FUSED_RETRY;
+                continue;
+            }
+            if (fused_now) ++fused_restarts;
+            if (p->profile && fused_now == (p->fused != 0) &&
+                (fused_now || p->m / 2 < h->last_m_eff)) {   // the timed work ran
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) {
                     S.spmv_ms += ms;
@@ -403,7 +433,7 @@ te_status run_solve(te_ctx* ctx, const te_matrix* H, Plan* p, cudaStream_t s, co
     S.quad_nodes = h->quad_nodes;
     S.eig_mcycles = 1e-6 * (double)h->eig_cycles;
     S.search_mcycles = 1e-6 * (double)h->search_cycles;
-    S.fused_restarts = p->fused ? h->restarts : 0;
+    S.fused_restarts = fused_restarts;
     S.err_bound = h->err_acc;
     S.t_reached = (t >= 0.0 ? 1.0 : -1.0) * h->t_now;
     if (h->breakdowns) S.flags |= TE_FLAG_BREAKDOWN;

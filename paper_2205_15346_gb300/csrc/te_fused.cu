@@ -149,6 +149,9 @@ __global__ void __launch_bounds__(256) k_lanczos_fused(Slices M, double2* __rest
     // written by earlier kernels only: every block reads the same values
     if (st->status != 0 || st->done != 0 || st->stop) return;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    // test aid (TE_OPT_TEST_FUSED_TIMEOUT): the last block leaves before the first
+    // barrier, so that the others' bounded wait runs out
+    const bool hold = st->test_hold != 0 && blockIdx.x == gridDim.x - 1;
     const double sign = st->sign, tol_rate = st->tol_rate;
     double scale_j = st->scale[0];
     double bp = 0.0;                                  // beta[j-1] * scale[j-1]
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(256) k_lanczos_fused(Slices M, double2* __rest
         }
         double b = block_sum(acc, sh);
         if (threadIdx.x == 0) part[blockIdx.x] = b;
+        if (hold) return;
         if (!grid_barrier(bar, gen, &ok_sh)) {
             ok = false;
             break;

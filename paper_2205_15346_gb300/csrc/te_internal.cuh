@@ -49,7 +49,7 @@ struct DevState {
     int32_t quad_max_levels;
     int32_t max_substeps;
     int32_t smallexp;        // TE_SMALLEXP_*
-    int32_t pad1;
+    int32_t test_hold;       // TE_OPT_TEST_FUSED_TIMEOUT: one block of the fused loop skips a barrier
     // progress of the solve
     double t_now;
     double prev_step;
@@ -151,6 +151,8 @@ struct Plan {
     double* partials_r = nullptr;    // reorthogonalisation scratch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec_unfused = nullptr;   // fused plans: the same restart as separate launches
+                                              // (run when the fused loop's barrier gave up)
     std::vector<cudaEvent_t> ev;     // TE_OPT_PROFILE: start/stop per Lanczos step
     size_t bytes = 0;
     bool in_use = false;

@@ -45,6 +45,8 @@ TE_QUAD_GAUSS = 1
 TE_REORTH_NONE = 0
 TE_REORTH_FULL = 1
 TE_OPT_PROFILE = 0x10
+TE_OPT_TEST_FUSED_TIMEOUT = 0x20
+TE_FLAG_FUSED_RETRY = 0x8
 TE_SMALLEXP_CHEB = 0
 TE_SMALLEXP_EIG = 1
 TE_FUSED_AUTO = 0

@@ -120,3 +120,33 @@ def test_barrier_wait_is_bounded(te, ctx):
         assert s["fused_restarts"] > 0 and s["err_bound"] <= 1e-8
     finally:
         te.te_matrix_free(H)
+
+
+def test_timed_out_fused_restart_is_rerun_unfused(te, ctx):
+    """A grid barrier of the fused loop that gives up no longer fails the solve: with
+    TE_OPT_TEST_FUSED_TIMEOUT one block of the first fused restart leaves before its
+    first barrier, the others' bounded wait runs out, and the library restores that
+    restart's starting state and runs it (and the rest of the solve) as separate
+    launches.  The result equals the oracle within 2 tol + 1e-12."""
+    import time
+    p = W.tfim_params(12, 83)
+    H = te.te_build_model(ctx, p)
+    try:
+        v0 = W.random_state(84, 1 << 12)
+        o = te.make_options()
+        o.flags |= te.TE_OPT_TEST_FUSED_TIMEOUT
+        a = time.perf_counter()
+        out, st, s = te.te_evolve(ctx, H, v0, 6.0, 1e-8, 40, o)
+        wall = time.perf_counter() - a
+        assert s == te.TE_OK
+        assert st["flags"] & te.TE_FLAG_FUSED_RETRY
+        assert st["fused_restarts"] == 0 and st["restarts"] >= 2
+        assert 0.5 < wall < 30.0                         # the bounded wait, then the retry
+        ref = krylov.evolve(models.build(p).to_scipy(), v0, 6.0, 1e-8, 40)
+        assert np.linalg.norm(out - ref.v) <= 2e-8 + 1e-12
+        # the plan keeps serving fused solves afterwards
+        out2, st2, _ = te.te_evolve(ctx, H, v0, 6.0, 1e-8, 40)
+        assert st2["fused_restarts"] == st2["restarts"] and not (st2["flags"] & te.TE_FLAG_FUSED_RETRY)
+        assert np.linalg.norm(out2 - ref.v) <= 2e-8 + 1e-12
+    finally:
+        te.te_matrix_free(H)
