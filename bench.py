@@ -568,7 +568,8 @@ def run_ours(args):
         k1_timing = "CUDA events around the fused Lanczos kernel of every restart inside the timed solves"
     else:
         k1_name = (("k_spmv_sellr" if info["sell_dict"] > 0 and info["sell_real"]
-                    else (f"k_spmv_sellv_async<{info['sell_async']}>" if info.get("sell_async")
+                    else ("k_spmv_sellv_pair" if info.get("sell_async") == 1
+                          else f"k_spmv_sellv_async<{info['sell_async']}>" if info.get("sell_async")
                           else "k_spmv_sellv") if info["sell_dict"] > 0 else "k_spmv_sell") +
                    " (K1: y = s H u_j - b u_{j-1}, Re<u_j,y> partials)")
         k1_timing = ("CUDA events around the Lanczos step m/2 product of every "

@@ -285,7 +285,8 @@ void te_matrix_free(te_matrix* H);
  * best of `repeats` launches after one warm-up) for work items of 1, 2, 3, 4, 6 and
  * 8 slices, and for a complex value table also with two slices per pass and with
  * the gathers staged in shared memory two or four entries ahead, and keeps the
- * fastest (te_matrix_info.sell_tpt,
+ * fastest (another form than the register-gather one only when it is at least 1 %
+ * faster) (te_matrix_info.sell_tpt,
  * sell_async; every candidate gives bitwise the same product).  The initial choice
  * is a fixed rule (about 1.5K stored entries per item, at most 4 slices).  Cached
  * solver plans of H are dropped (their scratch depends on the item size); returns
