@@ -255,11 +255,14 @@ __device__ void ts_table(double* tx, double* tw) {
 }
 
 // Chebyshev vectors v_k = T_k(T~) e_1 (three buffers rotated in shared memory),
-// extended until g is valid up to index K.
+// extended until g is valid up to index K.  Each v_k with k < nkeep is also kept
+// at keep + k * mcap, for the evaluation of omega at the chosen step.
 struct ChebState {
     double* v[3];
     int cur;                         // v[cur] = v_kdone, v[(cur + 2) % 3] = v_{kdone-1}
     int kdone;
+    double* keep;
+    int nkeep, mcap;
 };
 
 __device__ void cheb_extend(ChebState& cs, double* g, int K, int n, const double* alpha,
@@ -269,12 +272,15 @@ __device__ void cheb_extend(ChebState& cs, double* g, int K, int n, const double
         const double* vc = cs.v[cs.cur];
         const double* vp = cs.v[(cs.cur + 2) % 3];
         double* vn = cs.v[(cs.cur + 1) % 3];
+        double* kp = (cs.kdone + 1 < cs.nkeep) ? cs.keep + (size_t)(cs.kdone + 1) * cs.mcap : nullptr;
         for (int i = tid; i < n; i += nt) {
             double tv = (alpha[i] - b) * vc[i];
             if (i > 0) tv = fma(beta[i - 1], vc[i - 1], tv);
             if (i + 1 < n) tv = fma(beta[i], vc[i + 1], tv);
             tv *= a_inv;
-            vn[i] = (cs.kdone == 0) ? tv : 2.0 * tv - vp[i];
+            tv = (cs.kdone == 0) ? tv : 2.0 * tv - vp[i];
+            vn[i] = tv;
+            if (kp) kp[i] = tv;
         }
         __syncthreads();
         if (tid == 0) g[cs.kdone + 1] = vn[n - 1];
@@ -353,6 +359,12 @@ __device__ double integrate(const Small& F, const Quad& Qd, double a, double b, 
     return total;
 }
 
+// The Chebyshev vectors the step search computes are kept for omega while they
+// fit in this much shared memory (about 150 vectors at m = 40; a longer series
+// runs its recurrence again); the step kernel then still fits twice per SM.
+constexpr int kKeepBytes = 48 * 1024;
+__host__ __device__ constexpr int keep_vectors(int mcap) { return kKeepBytes / (8 * mcap); }
+
 // Shared-memory carve-up (16-byte aligned blocks first).
 struct Layout {
     double2* ph;     // mcap
@@ -369,6 +381,7 @@ struct Layout {
     double* v3;      // 3 * mcap: Chebyshev vectors
     double* g;       // kKcap: g_k
     double* jk;      // kKcap: J_k for omega
+    double* vk;      // keep_vectors(mcap) * mcap: T_k(T~) e_1 kept for omega
     double* tx;      // kTabNodes: unit tanh-sinh nodes
     double* tw;      // kTabNodes: their weights
     double* tv;      // kTabNodes: weighted integrand values of one round
@@ -398,11 +411,12 @@ __device__ Layout carve(double* smem, int mcap, int method) {
     L.tw = p; p += kTabNodes;
     L.tv = p; p += kTabNodes;
     if (method == TE_SMALLEXP_EIG) {
-        L.v3 = L.g = L.jk = nullptr;
+        L.v3 = L.g = L.jk = L.vk = nullptr;
     } else {
         L.v3 = p; p += 3 * (size_t)mcap;
         L.g = p; p += kKcap;
         L.jk = p; p += kKcap;
+        L.vk = p; p += (size_t)keep_vectors(mcap) * mcap;
     }
     L.ri = reinterpret_cast<int*>(p);
     return L;
@@ -495,6 +509,20 @@ __device__ bool ql_eigen(const Layout& L, int n, int* sh_mm, int* sh_nrot, int* 
 
 // One CTA per solve: CTA b works on st_base[b] (a batch of independent solves
 // sharing H launches one CTA per vector).
+// omega = exp(-i H_m tau) e_1 by the Chebyshev series (every thread of the block).
+// A one-piece series whose vectors fit the kept ones extends them as far as it
+// needs (a lucky breakdown evaluates none during the search) and sums them.
+__device__ bool omega_cheb(const Layout& L, ChebState& cs, int n, const Small& F, double tau,
+                           int mcap, double* sh_S) {
+    const double z = F.a * tau;
+    if (n > 1 && z <= kZPiece) {
+        const int K = min(bessel_terms(fmin(z, (double)kKcap)), kKcap - kMillerExtra - 1);
+        if (K < cs.nkeep && cs.kdone < K) cheb_extend(cs, L.g, K, n, L.al, L.be, F.inv_a, F.b);
+    }
+    return cheb_exp_e1(L.al, L.be, n, F.a, F.b, F.inv_a, tau, L.jk, L.v3, mcap, sh_S, L.om, L.vk,
+                       min(cs.kdone + 1, cs.nkeep));
+}
+
 __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, int mcap) {
     DevState* st = st_base + blockIdx.x;
     extern __shared__ double smem[];
@@ -564,9 +592,13 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
         cs.v[2] = L.v3 + 2 * mcap;
         cs.cur = 0;
         cs.kdone = 0;
+        cs.keep = L.vk;
+        cs.nkeep = keep_vectors(mcap);
+        cs.mcap = mcap;
         for (int i = tid; i < n; i += nt) {
             cs.v[0][i] = (i == 0) ? 1.0 : 0.0;
             cs.v[2][i] = 0.0;
+            L.vk[i] = cs.v[0][i];
         }
         if (tid == 0) L.g[0] = (n == 1) ? 1.0 : 0.0;
         __syncthreads();
@@ -672,8 +704,7 @@ __global__ void __launch_bounds__(TE_STEP_THREADS, 1) k_step(DevState* st_base, 
             }
             L.om[r] = make_double2(re, im);
         }
-    } else if (!cheb_exp_e1(L.al, L.be, n, F.a, F.b, F.inv_a, tau, L.jk, L.v3, mcap, &sh_S,
-                            L.om)) {
+    } else if (!omega_cheb(L, cs, n, F, tau, mcap, &sh_S)) {
         // a step longer than the series' pieces reach (only a lucky breakdown takes one)
         if (tid == 0) {
             st->status = TE_ERR_UNSUPPORTED;
@@ -718,7 +749,8 @@ int step_smem_bytes(int m) {
                        sizeof(double) * ((size_t)m * m + 8 * (size_t)m + 3 * kTabNodes) +
                        sizeof(int) * m;
     const size_t cheb = sizeof(double2) * 2 * m +
-                        sizeof(double) * (11 * (size_t)m + 2 * kKcap + 3 * kTabNodes) +
+                        sizeof(double) * (11 * (size_t)m + 2 * kKcap + 3 * kTabNodes +
+                                          (size_t)keep_vectors(m) * m) +
                         sizeof(int) * m;
     return (int)(eig > cheb ? eig : cheb);
 }
