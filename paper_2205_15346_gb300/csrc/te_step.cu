@@ -142,6 +142,9 @@ __device__ __forceinline__ double f_cheb(const Small& F, double tau) {
     double jp = 0.0, jc = 1e-300;    // J_{k+1}, J_k (unnormalised)
     double S2 = 0.0, re = 0.0, im = 0.0, j0 = 0.0;
     const double* g = F.g;
+    // |J_k| > kBig tested on the bit pattern (ordered like the magnitude), on the
+    // integer pipe instead of the FP64 pipe
+    const unsigned long long kBigBits = (unsigned long long)__double_as_longlong(kBig);
     // one step at index k: accumulate, then move to k - 1
 #define TE_ACC(k, q)                                                       \
     if ((k) >= first && (k) <= Kn) {                                        \
@@ -159,7 +162,7 @@ __device__ __forceinline__ double f_cheb(const Small& F, double tau) {
         t -= inv;                                                           \
     }
 #define TE_GUARD()                                                         \
-    if (fabs(jc) > kBig) {                                                  \
+    if (((unsigned long long)__double_as_longlong(jc) & 0x7fffffffffffffffull) > kBigBits) { \
         jc *= kSmall;                                                       \
         jp *= kSmall;                                                       \
         S2 *= kSmall;                                                       \
