@@ -80,8 +80,11 @@ def attainable_fp64(ctx, achieved_tf):
     and the kernel's fraction of it, beside the derived pipe peak."""
     from paper_2205_15346_gb300 import te
     rate = te.te_measure_fp64(ctx)
+    mma = te.te_measure_fp64_mma(ctx)
     return {"tflops": rate, "frac": achieved_tf / rate,
-            "how": "te_measure_fp64: independent DFMA chains, no memory traffic, after the timed region"}
+            "how": "te_measure_fp64: independent DFMA chains, no memory traffic, after the timed region",
+            "fp64_mma_tflops": mma,
+            "fp64_mma_how": "te_measure_fp64_mma: mma.sync m8n8k4 .f64 on independent tiles, after the timed region"}
 
 
 def measured_peaks():

@@ -315,6 +315,16 @@ te_status te_matrix_set_sell(te_ctx* ctx, te_matrix* H, int32_t slices_per_task,
  * TE_ERR_CUDA. */
 te_status te_measure_fp64(te_ctx* ctx, double* tflops);
 
+/* The FP64 rate of the GPU's FP64 matrix instruction (mma.sync m8n8k4 on .f64
+ * operands, 256 multiply-adds per warp instruction), in TFLOP/s, on independent
+ * accumulator tiles with no memory traffic.  The paper has no counterpart: it
+ * is the measurement that decides whether the recombination w = V_m omega or the
+ * orthogonalisation of Algorithm 1, written as small dense products, could run
+ * faster on it than on the FP64 vector pipe (te_measure_fp64).  Runs for about
+ * 0.2 s on the context's stream after the caller's queued work, allocates and
+ * frees a 1 MB scratch.  Errors: TE_ERR_INVALID_ARG (NULL argument), TE_ERR_CUDA. */
+te_status te_measure_fp64_mma(te_ctx* ctx, double* tflops);
+
 /* The grid barrier of the fused Lanczos loop (te_options.fused_lanczos), run
  * once over a cooperative grid of one 32-thread block per SM.  The paper has no
  * counterpart: this exists so that tests can see that the barrier's bounded

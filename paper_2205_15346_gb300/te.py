@@ -128,6 +128,7 @@ _SIGS = {
     "te_matrix_free": (None, [_P]),
     "te_matrix_tune": (C.c_int32, [_P, _P, C.c_int32, C.POINTER(C.c_double)]),
     "te_measure_fp64": (C.c_int32, [_P, C.POINTER(C.c_double)]),
+    "te_measure_fp64_mma": (C.c_int32, [_P, C.POINTER(C.c_double)]),
     "te_matrix_set_sell": (C.c_int32, [_P, _P, C.c_int32, C.c_int32]),
     "te_fused_barrier_check": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_int32),
                                            C.POINTER(C.c_double)]),
@@ -417,6 +418,13 @@ def te_measure_fp64(ctx) -> float:
     """The FP64 FMA rate this GPU sustains on independent chains (TFLOP/s)."""
     r = C.c_double()
     _check(ctx, lib().te_measure_fp64(ctx, C.byref(r)))
+    return r.value
+
+
+def te_measure_fp64_mma(ctx) -> float:
+    """The FP64 rate of the GPU's FP64 matrix instruction (mma.sync m8n8k4, TFLOP/s)."""
+    r = C.c_double()
+    _check(ctx, lib().te_measure_fp64_mma(ctx, C.byref(r)))
     return r.value
 
 

@@ -177,6 +177,15 @@ def test_measure_fp64_rate_is_within_the_pipe_peak(te, ctx):
     assert 0.3 * peak < r <= 1.02 * peak, (r, peak)
 
 
+def test_measure_fp64_mma_rate_is_positive_and_bounded(te, ctx):
+    """te_measure_fp64_mma executes its matrix instructions: a positive rate, below
+    the nominal FP64 rate of the fastest FP64 tensor units of this GPU family
+    (the probe decides between the two FP64 paths; it asserts neither is faster)."""
+    r = te.te_measure_fp64_mma(ctx)
+    v = te.te_measure_fp64(ctx)
+    assert 0.0 < r < 100.0 and v > 0.0, (r, v)
+
+
 @pytest.mark.parametrize("params", [W.xxzdm_params(14, 2), W.bose_params(10, 6, 4),
                                     W.xxzdm_params(5, 6)],
                          ids=["xxzdm14", "bose10_6", "xxzdm5"])
