@@ -120,7 +120,7 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s, bool fused,
             e = p->lanes ? launch_spmv_lanczos(H, p->lanes, x, xprev, y, p->st, j, 0, p->partials,
                                                p->grid_k1, s)
                          : launch_spmv_sell(H, x, p->S + (size_t)j * d, xprev, y, p->st, j, 0,
-                                            p->partials, s);
+                                            p->partials, s, p->grid_k1);
         if (timed && e == cudaSuccess)
             e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
         if (e != cudaSuccess) break;
@@ -159,7 +159,7 @@ te_status capture_restart(te_ctx* ctx, Plan* p, cudaStream_t s, bool fused,
 }
 
 te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
-                      int fused, cudaStream_t s, Plan** out, int ns = 0) {
+                      int fused, cudaStream_t s, Plan** out, int ns = 0, int share = 0) {
     Plan* p = new Plan();
     p->ctx = ctx;
     p->H = H;
@@ -176,6 +176,8 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
     p->lanes = lanes;
     p->d = H->d;
     p->grid_k1 = lanes ? spmv_grid(lanes, H->d, ctx->num_sms) : H->sell_grid;
+    p->share = share;
+    if (share && !lanes && p->grid_k1 >= 2 * ctx->num_sms) p->grid_k1 -= ctx->num_sms;
     const int64_t want = (H->d + TE_BLOCK - 1) / TE_BLOCK;
     p->grid_stream = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 8);
     p->grid_reorth = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->num_sms * 2);
@@ -230,19 +232,20 @@ te_status create_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int pr
 // Take a cached idle plan that fits, or build one (dropping idle plans if the
 // device runs out of memory).
 te_status acquire_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int profile, int lanes,
-                       int fused, cudaStream_t s, Plan** out) {
+                       int fused, cudaStream_t s, Plan** out, int share = 0) {
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         for (Plan* p : ctx->plans)
             if (!p->in_use && p->matrix_id == H->id && p->m == m && p->reorth == reorth &&
-                p->profile == profile && p->lanes == lanes && p->fused == fused) {
+                p->profile == profile && p->lanes == lanes && p->fused == fused &&
+                p->share == share) {
                 p->in_use = true;
                 *out = p;
                 return TE_OK;
             }
     }
     Plan* p = nullptr;
-    te_status st = create_plan(ctx, H, m, reorth, profile, lanes, fused, s, &p);
+    te_status st = create_plan(ctx, H, m, reorth, profile, lanes, fused, s, &p, 0, share);
     if (st == TE_ERR_OOM) {
         std::vector<Plan*> idle;
         {
@@ -254,7 +257,7 @@ te_status acquire_plan(te_ctx* ctx, const te_matrix* H, int m, int reorth, int p
         }
         cudaStreamSynchronize(s);
         for (Plan* q : idle) free_plan(q);
-        st = create_plan(ctx, H, m, reorth, profile, lanes, fused, s, &p);
+        st = create_plan(ctx, H, m, reorth, profile, lanes, fused, s, &p, 0, share);
     }
     if (st) return st;
     p->in_use = true;
@@ -1328,6 +1331,9 @@ void te_request_free(te_request* r) {
     if (!queued_removed && r->state.load() == 1) {
         std::unique_lock<std::mutex> lk(r->mu);
         r->cv.wait(lk, [&] { return r->state.load() == 2; });
+    } else {
+        // a publisher that set state 2 may still hold the lock (it notifies under it)
+        std::lock_guard<std::mutex> lk(r->mu);
     }
     if (ctx) cudaSetDevice(ctx->device);
     if (r->v_in_dev) dev_free(r->ctx, r->v_in_dev);
@@ -1386,9 +1392,11 @@ void worker_loop(te_ctx* ctx) {
         } else {
             Plan* p = nullptr;
             const int lanes = r->opt.spmv_lanes;
+            // beside the batches, a large request's SpMV leaves them a block slot per SM
             res = acquire_plan(ctx, r->H, r->m, r->opt.reorth,
                                (r->opt.flags & TE_OPT_PROFILE) ? 1 : 0, lanes,
-                               want_fused(ctx, r->H, r->opt), s, &p);
+                               want_fused(ctx, r->H, r->opt), s, &p,
+                               ctx->serve_mode == TE_SERVE_BATCH ? 1 : 0);
             if (res == TE_OK) {
                 res = run_solve(ctx, r->H, p, s, r->v_in_dev, r->t, r->tol, r->opt, r->v_out_dev,
                                 true, &S, &r->cancel);
@@ -1399,23 +1407,28 @@ void worker_loop(te_ctx* ctx) {
                 msg = ctx->err;
             }
         }
+        // publish first, then free the lane: a request finishes (as its owner sees it)
+        // before the next one starts.  The notification is sent under the request's
+        // lock, and r is not touched after that lock is released (its owner may free it).
+        const int64_t footprint = (int64_t)r->footprint;
         {
             std::lock_guard<std::mutex> lk(ctx->qmu);
-            if (counted) {
-                ctx->in_use -= (int64_t)r->footprint;
-                ctx->solo_running -= 1;
-            }
             ctx->pending -= 1;
         }
-        ctx->qcv.notify_all();
         {
             std::lock_guard<std::mutex> lk(r->mu);
             r->stats = S;
             r->result = res;
             r->err = res == TE_ERR_CANCELLED ? std::string("request cancelled") : msg;
             r->state.store(2);
+            r->cv.notify_all();
         }
-        r->cv.notify_all();
+        if (counted) {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            ctx->in_use -= footprint;
+            ctx->solo_running -= 1;
+        }
+        ctx->qcv.notify_all();
     }
     if (s) cudaStreamDestroy(s);
 }

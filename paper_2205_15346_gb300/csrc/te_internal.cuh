@@ -157,6 +157,10 @@ struct Plan {
     size_t bytes = 0;
     bool in_use = false;
     int grid_k1 = 0, grid_stream = 0, grid_reorth = 0;
+    // 1: the plan of a large request served beside the batches; its SpMV leaves one
+    // block slot per SM free (grid_k1 one block per SM below full occupancy), so the
+    // batches' kernels start without waiting for the SpMV's resident blocks to end
+    int share = 0;
     // fused Lanczos loop (te_fused.cu): one cooperative kernel per restart
     int fused = 0;
     int fused_grid = 0, fused_threads = 0;
@@ -258,9 +262,11 @@ int sell_grid(int64_t nslices, int num_sms, int form);   // 0 full, 1 indexed, 2
 int sell_async_grid(int64_t nslices, int num_sms, int trip);   // the staged indexed product
 cudaError_t sell_prepare();                     // shared-memory limit of the staged product
 int64_t sell_partials(const te_matrix* H);
+// grid > 0 overrides H->sell_grid (the kernel takes its work from a counter, so any
+// grid computes the same product)
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,
-                             double* partials, cudaStream_t s);
+                             double* partials, cudaStream_t s, int grid = 0);
 cudaError_t launch_gather(const double2* src, const int32_t* map, int64_t d, double2* dst,
                           double* dsum, int num_sms, cudaStream_t s);
 // fused Lanczos loop (te_fused.cu): shape of its cooperative grid (false: H too

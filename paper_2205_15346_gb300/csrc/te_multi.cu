@@ -794,8 +794,11 @@ struct ServeEngine {
     std::vector<std::pair<int64_t, int64_t>> holes;   // free arena segments (offset, length)
     bool dirty = true;              // composition changed since the last capture
 
-    te_status init(te_ctx* c, int m_max, int64_t capacity, int cls) {
+    int cls = 0;                    // 0: small batch, 1: medium batch
+
+    te_status init(te_ctx* c, int m_max, int64_t capacity, int cls_) {
         ctx = c;
+        cls = cls_;
         depth = m_max;
         cap = capacity / 32 * 32;
         npart = (size_t)(cap / 32 + 2 * TE_MULTI_MAX + 1);
@@ -943,6 +946,9 @@ te_status serve_compose(ServeEngine& E) {
     mp.nchunks = cs[n];
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_multi, TE_BLOCK, 0);
+    // the medium batch's grouped SpMV (its blocks stay resident for the whole
+    // product) leaves one block slot per SM to the small batch
+    if (E.cls == 1 && occ >= 2) occ -= 1;
     mp.grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>((mp.ntasks + 7) / 8,
                                                                 (int64_t)std::max(occ, 1) * ctx->num_sms));
     mp.grid_stream = grid_stream;
@@ -969,13 +975,15 @@ void serve_publish(te_request* r, te_status res, const te_stats& S, const std::s
         r->ctx->pending -= 1;
     }
     {
+        // notified under the lock: r is not touched after it is released (its owner
+        // may free it then)
         std::lock_guard<std::mutex> lk(r->mu);
         r->stats = S;
         r->result = res;
         r->err = msg;
         r->state.store(2);
+        r->cv.notify_all();
     }
-    r->cv.notify_all();
 }
 
 // Finished or failed slot i: its result leaves the arena (back to the caller's

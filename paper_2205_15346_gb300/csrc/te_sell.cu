@@ -706,29 +706,30 @@ int sell_async_grid(int64_t nslices, int num_sms, int trip) {
 // Re x + Im x.
 cudaError_t launch_spmv_sell(const te_matrix* H, const double2* x, const double* xs,
                              const double2* xprev, double2* y, DevState* st, int j, int mode,
-                             double* partials, cudaStream_t s) {
+                             double* partials, cudaStream_t s, int grid) {
+    const int g = grid > 0 ? grid : H->sell_grid;
     if (H->sell_idx && H->dict_real) {
         const RealIndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->sell_diag};
-        k_spmv_sellr<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+        k_spmv_sellr<<<g, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
                                                       H->sell_tpt, st, j, mode, partials);
     } else if (H->sell_idx) {
         const IndexedSlices M{H->sell_off, H->sell_col, H->sell_idx, H->dict_a, H->dict_pq,
                               H->sell_diag};
         if (H->sell_async == 1)
-            k_spmv_sellv_pair<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+            k_spmv_sellv_pair<<<g, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
                                                                H->sell_tpt, st, j, mode, partials);
         else if (H->sell_async == 4)
-            k_spmv_sellv_async<4><<<H->sell_grid, TE_BLOCK, async_smem(4), s>>>(
+            k_spmv_sellv_async<4><<<g, TE_BLOCK, async_smem(4), s>>>(
                 M, x, xs, xprev, y, H->d, H->nslices, H->sell_tpt, st, j, mode, partials);
         else if (H->sell_async == 2)
-            k_spmv_sellv_async<2><<<H->sell_grid, TE_BLOCK, async_smem(2), s>>>(
+            k_spmv_sellv_async<2><<<g, TE_BLOCK, async_smem(2), s>>>(
                 M, x, xs, xprev, y, H->d, H->nslices, H->sell_tpt, st, j, mode, partials);
         else
-            k_spmv_sellv<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+            k_spmv_sellv<<<g, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
                                                           H->sell_tpt, st, j, mode, partials);
     } else {
         const FullSlices M{H->sell_off, H->sell_col, H->sell_a, H->sell_pq};
-        k_spmv_sell<<<H->sell_grid, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
+        k_spmv_sell<<<g, TE_BLOCK, 0, s>>>(M, x, xs, xprev, y, H->d, H->nslices,
                                                      H->sell_tpt, st, j, mode, partials);
     }
     return cudaGetLastError();
