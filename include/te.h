@@ -544,7 +544,11 @@ te_status te_evolve_multi(te_ctx* ctx, int32_t n, const te_matrix* const* H,
  *     GPU by itself) run in the large lane instead: one at a time, first come
  *     first served, as a solo solve on its own stream beside the batches (stream
  *     priorities: small batch highest, large lane next, medium batch lowest), so
- *     that large requests neither slow each other down nor wait behind small ones.  Requests with reorthogonalisation, the CSR kernel (spmv_lanes),
+ *     that large requests neither slow each other down nor wait behind small ones.
+ *     The large lane's sparse products and the medium batch's run one block per
+ *     SM below full occupancy, leaving the small batch room to start at once.  A
+ *     large request is reported finished before the next one starts.  Requests
+ *     with reorthogonalisation, the CSR kernel (spmv_lanes),
  *     TE_OPT_PROFILE, m above the arena depth or d above its capacity take
  *     the large lane too.
  *   TE_SERVE_SOLO: up to 8 worker threads each admit the oldest queued request
