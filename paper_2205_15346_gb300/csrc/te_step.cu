@@ -268,25 +268,34 @@ struct ChebState {
     int nkeep, mcap;
 };
 
+static_assert(TE_M_MAX <= TE_STEP_THREADS, "the step kernel keeps one Krylov row per thread");
+
 __device__ void cheb_extend(ChebState& cs, double* g, int K, int n, const double* alpha,
                             const double* beta, double a_inv, double b) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    // one row per thread (n <= TE_M_MAX <= blockDim.x): the row's coefficients stay
+    // in registers, (alpha_i - b) is formed once, and the owner of row n - 1 writes
+    // g_k itself, so a step needs one block barrier.  Three rotating buffers make
+    // that barrier enough: step k reads v_k (neighbouring rows) and v_{k-1} (own
+    // row) and writes v_{k+1} over v_{k-2}, which no thread still reads.
+    const int i = threadIdx.x;
+    const bool own = i < n;
+    const double ab = own ? alpha[i] - b : 0.0;
+    const double bl = (own && i > 0) ? beta[i - 1] : 0.0;
+    const double br = (own && i + 1 < n) ? beta[i] : 0.0;
     while (cs.kdone < K) {
         const double* vc = cs.v[cs.cur];
         const double* vp = cs.v[(cs.cur + 2) % 3];
         double* vn = cs.v[(cs.cur + 1) % 3];
-        double* kp = (cs.kdone + 1 < cs.nkeep) ? cs.keep + (size_t)(cs.kdone + 1) * cs.mcap : nullptr;
-        for (int i = tid; i < n; i += nt) {
-            double tv = (alpha[i] - b) * vc[i];
-            if (i > 0) tv = fma(beta[i - 1], vc[i - 1], tv);
-            if (i + 1 < n) tv = fma(beta[i], vc[i + 1], tv);
+        if (own) {
+            double tv = ab * vc[i];
+            if (i > 0) tv = fma(bl, vc[i - 1], tv);
+            if (i + 1 < n) tv = fma(br, vc[i + 1], tv);
             tv *= a_inv;
             tv = (cs.kdone == 0) ? tv : 2.0 * tv - vp[i];
             vn[i] = tv;
-            if (kp) kp[i] = tv;
+            if (cs.kdone + 1 < cs.nkeep) cs.keep[(size_t)(cs.kdone + 1) * cs.mcap + i] = tv;
+            if (i == n - 1) g[cs.kdone + 1] = tv;
         }
-        __syncthreads();
-        if (tid == 0) g[cs.kdone + 1] = vn[n - 1];
         cs.cur = (cs.cur + 1) % 3;
         cs.kdone += 1;
         __syncthreads();
